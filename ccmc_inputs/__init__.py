@@ -1,0 +1,112 @@
+"""Seeded, synthetic inputs shared by the CUDA library's callers and the oracle.
+
+This module holds workload descriptions and input generators only: no part of
+the CCMC step lives here.  The paper's own systems (water, benzene) need
+integrals that are not available, so the workloads are a uniform electron gas
+(closed-form integrals) and a synthetic molecule-like Hamiltonian generated
+from a fixed seed.
+"""
+from __future__ import annotations
+
+import copy
+
+import numpy as np
+
+# Run parameters common to every workload.
+COMMON = dict(
+    d0_init=100.0,        # initial weight on the reference (unit-weight particles, Sec. II)
+    shift_a=10,           # steps between shift updates
+    zeta=0.05,            # shift damping
+    spawn_cutoff=2.0 ** -7,
+    a_thresh=1.0,         # multi-spawn threshold (the paper uses 1, Sec. IV.C)
+    fnc=False,
+    multispawn=False,
+    replica=0,
+    precision="fp64",
+)
+
+WORKLOADS = {
+    # UEG 14 e / 38 spin-orbitals (19 plane waves), CCSD, original sampling
+    "ueg14_m38_ccsd": dict(kind="ueg", nel=14, nso=38, rs=1.0, lmax=2, target_pop=2.0e4,
+                           tau=0.01, nsteps=200, seed=1),
+    # UEG 14 e / 114 spin-orbitals (57 plane waves), CCSDT, full non-composite + multi-spawn
+    "ueg14_m114_ccsdt_fnc_ms": dict(kind="ueg", nel=14, nso=114, rs=1.0, lmax=3, target_pop=1.0e6,
+                                    tau=0.005, nsteps=2000, seed=1, fnc=True, multispawn=True),
+    # synthetic molecule: 20 e in 41 spatial orbitals (82 spin-orbitals), CCSDTQ
+    "mol20_m82_ccsdtq": dict(kind="generic", nel=20, norb=41, lmax=4, target_pop=1.0e7,
+                             tau=0.005, nsteps=50, seed=1, molecule_seed=7),
+    # UEG 54 e / 162 spin-orbitals (81 plane waves), CCSD, FP32 matrix elements
+    "ueg54_m162_ccsd_fp32": dict(kind="ueg", nel=54, nso=162, rs=1.0, lmax=2, target_pop=1.0e8,
+                                 tau=0.01, nsteps=50, seed=1, precision="fp32"),
+}
+
+
+def workload(name: str, **overrides) -> dict:
+    """A complete parameter dictionary for one named workload."""
+    w = copy.deepcopy(COMMON)
+    w.update(WORKLOADS[name])
+    w.update(overrides)
+    w["name"] = name
+    return w
+
+
+def batched_replicas(n: int = 64) -> list[dict]:
+    """Replica r: M in {38, 54, 66, 114} x r_s in {0.5, 1, 2, 5} by r mod 16,
+    CCSD when floor(r/16) is even else CCSDT, target 10^(4 + r mod 3),
+    seed 1000 + r."""
+    out = []
+    ms = [38, 54, 66, 114]
+    rss = [0.5, 1.0, 2.0, 5.0]
+    for r in range(n):
+        c = r % 16
+        w = copy.deepcopy(COMMON)
+        w.update(kind="ueg", nel=14, nso=ms[c // 4], rs=rss[c % 4], lmax=2 if (r // 16) % 2 == 0 else 3,
+                 target_pop=10.0 ** (4 + r % 3), tau=0.01, nsteps=100, seed=1000 + r, replica=r,
+                 name=f"batched_r{r}")
+        out.append(w)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Synthetic molecule-like Hamiltonian
+# ---------------------------------------------------------------------------
+
+
+def molecule_fock_levels(norb: int = 41, nocc: int = 10) -> np.ndarray:
+    """Orbital energies spaced like a water-dimer-sized basis: two deep core
+    levels (fewer if nocc < 2), the remaining occupied levels evenly in
+    [-1.4, -0.45] and the virtual levels evenly in [0.15, 3.0] hartree."""
+    ncore = min(2, nocc)
+    core = np.array([-20.6, -20.5])[:ncore]
+    val = np.linspace(-1.4, -0.45, nocc - ncore)
+    virt = np.linspace(0.15, 3.0, norb - nocc)
+    return np.concatenate([core, val, virt])
+
+
+def molecule_integrals(norb: int = 41, nocc: int = 10, seed: int = 7, scale: float = 1.0):
+    """Return (h1[norb,norb], eri[norb,norb,norb,norb]) with 8-fold symmetric
+    chemists' integrals (pq|rs) = scale g exp(-(|p-q| + |r-s|)/8), g ~ N(0,1)
+    drawn in canonical order (p>=q, r>=s, pq>=rs) from PCG64(seed), and h1
+    chosen so that the closed-shell Fock matrix of the lowest nocc orbitals is
+    diagonal with the levels of molecule_fock_levels:
+    h_pq = e_p d_pq - sum_j [2 (pq|jj) - (pj|jq)]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    eri = np.zeros((norb,) * 4)
+    for p in range(norb):
+        for q in range(p + 1):
+            pq = p * (p + 1) // 2 + q
+            for r in range(norb):
+                for s in range(r + 1):
+                    rs_ = r * (r + 1) // 2 + s
+                    if rs_ > pq:
+                        continue
+                    v = scale * rng.standard_normal() * np.exp(-((p - q) + (r - s)) / 8.0)
+                    for a, b, c, d in ((p, q, r, s), (q, p, r, s), (p, q, s, r), (q, p, s, r),
+                                       (r, s, p, q), (s, r, p, q), (r, s, q, p), (s, r, q, p)):
+                        eri[a, b, c, d] = v
+    eps = molecule_fock_levels(norb, nocc)
+    occ = np.arange(nocc)
+    g = 2.0 * np.einsum("pqjj->pq", eri[:, :, occ][:, :, :, occ]) - np.einsum("pjjq->pq", eri[:, occ][:, :, occ])
+    h1 = np.diag(eps) - g
+    h1 = 0.5 * (h1 + h1.T)
+    return h1, eri
