@@ -50,13 +50,14 @@ def _mean_step(s, keep, pops, lst, K, tau, shift, fnc, ms):
 CASES = [
     ("mol", 0, 0), ("mol", 1, 0), ("mol", 1, 1), ("mol", 0, 1),
     ("ueg", 0, 0), ("ueg", 1, 1),
+    ("mol-negref", 0, 0), ("mol-negref", 1, 1),
 ]
 
 
 @pytest.mark.parametrize("kind,fnc,ms", CASES)
 def test_one_step_mean_equals_exact_action(kind, fnc, ms):
     tau, shift = 0.01, 0.3
-    if kind == "mol":
+    if kind.startswith("mol"):
         h1, eri = tiny_molecule(norb=5, nocc=2, seed=11, scale=0.3)
         ham = brute.GenericBrute(4, h1, eri)
         s = oracle.System.generic(4, h1, eri, 2)
@@ -68,6 +69,8 @@ def test_one_step_mean_equals_exact_action(kind, fnc, ms):
     efci, dets, H = brute.fci_energy(ham)
     rng = np.random.default_rng(3)
     lst, keep, pops = _random_list(s, dets, rng, 40.0)
+    if kind == "mol-negref":
+        pops[0] = -pops[0]          # a negative reference weight (overall sign of Psi)
     amps = {d: p / 65536 for d, p in zip(keep[1:], pops[1:])}
     exact = brute.exact_step_change(ham, dets, H, amps, pops[0] / 65536, tau, shift, s.ehf(), s.lmax)
     mean, se = _mean_step(s, keep, pops, lst, K, tau, shift, fnc, ms)
