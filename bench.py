@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Benchmark of the CCMC time step (samples/s and annihilated keys/s).
+
+Default workload: 14-electron uniform electron gas in 114 spin-orbitals,
+CCSDT, full non-composite + multi-spawn sampling, 10^6 target population,
+dtau = 0.005, FP64 (the paper's improved samplers, Sec. IV.B-C).  The
+wavefunction is grown from the reference to the target population (untimed),
+then W warm-up steps and K timed steps follow, each timed with CUDA events on
+the library's stream and with L2 flushed between steps.
+
+A "step" is one full CCMC time step: a1 scans, a2-a5 sampling/collapse/
+spawn/death, a6 non-composite sweep with multi-spawn, a7 radix sort, a8 key
+reduction, a9 merge, a10 estimators.  value = (cluster samples + non-composite
+visits) per second over the timed steps; annihilated keys/s counts the
+spawned records entering the sort.
+
+--impl reference times the CPU oracle (single host core) on bounded slices of
+the same workload at its target size.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CCMC cluster samples/sec/GPU + annihilated keys/sec; % of HBM roofline"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per phase (what the method itself must move)
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(phase: str, recs: list, nw: int) -> float:
+    """Per-step algorithmic bytes of a phase, averaged over the records.
+    List entry B_e = 8K (bits) + 8 (key) + 8 (population); a spawned record is
+    16 B (key + population).  The sort moves each record once in and once out;
+    passes beyond that are implementation overhead."""
+    be = 8 * nw + 16
+    out = []
+    for r in recs:
+        n = r["n_visit"] if r["n_visit"] else r["nocc_after"]
+        sp = r["n_spawned"]
+        if phase == "scan":
+            b = n * 8 + n * 8
+        elif phase == "sample":
+            b = r["n_sel"] * 0.97 * be + sp * 16
+        elif phase == "attempts":
+            b = r["n_attempts"] * be + sp * 16
+        elif phase == "sort":
+            b = sp * 32
+        elif phase == "reduce":
+            b = sp * 16 + r["n_keys"] * 16
+        elif phase == "merge":
+            b = n * be + r["n_keys"] * 16 + r["nocc_after"] * be
+        else:
+            b = 0
+        out.append(b)
+    return sum(out) / max(1, len(out))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_state(w):
+    """The workload at its target size, made by the oracle: every excitor of
+    the truncated space occupied with seeded populations summing to the
+    target (the oracle enumerates the space with its excitation generator)."""
+    import numpy as np
+
+    import oracle
+    from ccmc_inputs import synthetic_populations
+
+    so = oracle.System.ueg(w["nel"], w["nso"], w["rs"], w["lmax"])
+    keys = so.space_keys(w["lmax"], expand_top=False)
+    dets = [so.unrank(int(k)) for k in keys]
+    levels = [so.level(d) for d in dets]
+    bits = np.stack([so.to_words(d) for d in dets])
+    pops = synthetic_populations(levels, w["target_pop"], seed=21)
+    sim = oracle.Sim(so, tau=w["tau"], target_pop=w["target_pop"], d0_init=w["d0_init"], shift_a=w["shift_a"],
+                     zeta=w["zeta"], spawn_cutoff=w["spawn_cutoff"], fnc=w["fnc"], multispawn=w["multispawn"],
+                     a_thresh=w["a_thresh"], seed=w["seed"])
+    sim.set_list_words(bits, pops)
+    sim.set_state(1500, -0.35, True, w["target_pop"])
+    return sim, len(keys)
+
+
+def oracle_slices(sim, n_occ, nslices, count, it0=1500):
+    """Times `count` slices, each 1/nslices of one full step's visits and
+    cluster samples (propagation only).  Returns (samples, seconds, spawned)."""
+    samples, secs, spawned = 0, 0.0, 0
+    n_sel = None
+    for k in range(count):
+        q = k % nslices
+        sim.set_state(it0 + k // nslices, -0.35, True, 1.0)
+        if n_sel is None:
+            r0 = sim.sample_range(0, 0, 0, 0)
+            n_sel = r0.n_sel
+        i_lo, i_hi = q * n_occ // nslices, (q + 1) * n_occ // nslices
+        g_lo, g_hi = q * n_sel // nslices, (q + 1) * n_sel // nslices
+        t = time.perf_counter()
+        r = sim.sample_range(i_lo, i_hi, g_lo, g_hi)
+        secs += time.perf_counter() - t
+        samples += (i_hi - i_lo) + (g_hi - g_lo)
+        spawned += r.n_spawned
+    return samples, secs, spawned
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sim, n_occ = oracle_state(w)
+    nslices = 20
+    oracle_slices(sim, n_occ, nslices, args.warmup)
+    samples, secs, spawned = oracle_slices(sim, n_occ, nslices, args.steps)
+    v = samples / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "keys_per_s": spawned / secs,
+        "config": {"workload": w["name"], "electrons": w["nel"], "spin_orbitals": w["nso"],
+                   "truncation": w["lmax"], "target_pop": w["target_pop"], "tau": w["tau"],
+                   "sampling": "fnc+multispawn" if w["fnc"] else "original"},
+        "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} slices of 1/{nslices} of a full step (visits + cluster samples, "
+                                   f"propagation only) on the oracle-made full-space state, N_total = target"},
+        "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, w):
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import paper_1807_03749_gb300 as ccmc
+
+    stream = torch.cuda.Stream()
+    # independent replica per rank (replicas only: the path is single-GPU)
+    ctx = ccmc.from_workload(w, replica=rank, stream=stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    # growth to the target population (untimed)
+    t_grow = time.perf_counter()
+    grown = 0
+    reached = None
+    while grown < args.grow_max:
+        ctx.step(w["shift_a"])
+        grown += w["shift_a"]
+        it, shift, vary, nprev = ctx.get_state()
+        if vary and reached is None:
+            reached = grown
+        if reached is not None and grown >= reached + args.equilibrate:
+            break
+    ctx.sync()
+    t_grow = time.perf_counter() - t_grow
+    ctx.records()
+
+    def timed(nsteps):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
+        with torch.cuda.stream(stream):
+            for k in range(nsteps):
+                flush.fill_(k)
+                starts[k].record(stream)
+                ctx.step(1)
+                ends[k].record(stream)
+        stream.synchronize()
+        return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+    timed(args.warmup)
+    ctx.records()
+    _, _, launches0 = ctx.phase_times()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = timed(args.steps)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    recs = ctx.records()
+    _, _, launches1 = ctx.phase_times()
+    ms_total = sum(times)
+    samples = sum(r["n_sel"] + r["n_visit"] for r in recs)
+    keys = sum(r["n_spawned"] for r in recs)
+    if dist:
+        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        c = torch.tensor([samples, keys], device="cuda", dtype=torch.float64)
+        dist.all_reduce(c)
+        samples_all, keys_all = float(c[0].item()), float(c[1].item())
+    else:
+        ms_max, samples_all, keys_all = ms_total, float(samples), float(keys)
+
+    # per-phase timing pass (events between phases, one step at a time)
+    ctx.profile(True)
+    with torch.cuda.stream(stream):
+        for k in range(args.profile_steps):
+            flush.fill_(k)
+            ctx.step(1)
+    stream.synchronize()
+    pms, plaunch, _ = ctx.phase_times()
+    ctx.profile(False)
+    precs = ctx.records()
+    dom = max(pms, key=lambda p: pms[p])
+    dom_ms = pms[dom] / max(1, args.profile_steps)
+    alg = algorithmic_bytes(dom, precs, ctx.nw)
+    hbm, src = peaks()
+    achieved = alg / (dom_ms * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", f"traffic_{w['name']}.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get(dom)
+        except Exception:
+            traffic = None
+
+    # end-to-end through the public API with host buffers: upload the excip
+    # list, one step, download the list and the estimators
+    bits, _, pop = ctx.get_list()
+    e2e_steps = args.e2e_steps
+    h2d = d2h = 0
+    e2e_samples = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        ctx.set_list(bits, pop)
+        h2d += bits.nbytes + pop.nbytes
+        ctx.step(1)
+        bits, keys_h, pop = ctx.get_list()
+        en = ctx.energy()
+        d2h += bits.nbytes + keys_h.nbytes + pop.nbytes + 40
+    torch.cuda.synchronize()
+    e2e_secs = time.perf_counter() - t0
+    erecs = ctx.records()
+    e2e_samples = sum(r["n_sel"] + r["n_visit"] for r in erecs[-e2e_steps:])
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    value = samples_all / (ms_max * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "keys_per_s": keys_all / (ms_max * 1e-3),
+        "config": {"workload": w["name"], "electrons": w["nel"], "spin_orbitals": w["nso"], "truncation": w["lmax"],
+                   "target_pop": w["target_pop"], "tau": w["tau"],
+                   "sampling": "fnc+multispawn" if w["fnc"] else "original",
+                   "state": f"grown from HF for {grown} steps ({t_grow:.1f} s), shift varying",
+                   "n_occ": recs[-1]["nocc_after"], "n_total": recs[-1]["ntot_after"] / 65536.0,
+                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
+                     "phase_ms_per_step": {k: v / max(1, args.profile_steps) for k, v in pms.items()},
+                     "algorithmic_bytes_per_launch": alg},
+        "clocks": clk,
+        "e2e": {"value": e2e_samples / e2e_secs, "unit": "samples/s", "h2d_bytes_per_step": h2d // max(1, e2e_steps),
+                "d2h_bytes_per_step": d2h // max(1, e2e_steps)},
+        "gpu_launches": int(launches1 - launches0),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(w):
+    """The oracle on one host core, on slices of one full step at the target
+    size (about 10 s of CPU work)."""
+    try:
+        sim, n_occ = oracle_state(w)
+    except Exception as e:  # the oracle is a reported baseline only
+        return {"value": None, "unit": "samples/s", "cores": 1, "kind": "oracle", "sample": f"unavailable: {e}"}
+    nslices = 20
+    samples, secs, done = 0, 0.0, 0
+    while secs < 8.0 and done < 4:
+        s, t, _ = oracle_slices(sim, n_occ, nslices, nslices, it0=1500 + done)
+        samples += s
+        secs += t
+        done += 1
+    return {"value": samples / secs, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} full steps of visits + cluster samples (propagation only, in {nslices} slices each) "
+                      f"on the oracle-made full-space state at N_total = target, {secs:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ueg14_m114_ccsdt_fnc_ms")
+    ap.add_argument("--grow-max", type=int, default=8000)
+    ap.add_argument("--equilibrate", type=int, default=100)
+    ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    from ccmc_inputs import workload
+
+    w = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

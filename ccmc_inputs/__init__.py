@@ -110,3 +110,23 @@ def molecule_integrals(norb: int = 41, nocc: int = 10, seed: int = 7, scale: flo
     h1 = np.diag(eps) - g
     h1 = 0.5 * (h1 + h1.T)
     return h1, eri
+
+
+def synthetic_populations(levels, n_total: float, seed: int, ref_fraction: float = 0.2) -> np.ndarray:
+    """Seeded fixed-point populations (multiples of 2^-16) for a list whose
+    first entry is the reference: the reference holds ref_fraction of
+    n_total; the others share the rest with lognormal magnitudes that fall by
+    10x per excitation level above 2, random signs, and at least one particle
+    each (the occupation threshold of a converged list)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    levels = np.asarray(levels)
+    n = len(levels)
+    w = np.exp(rng.standard_normal(n)) * 10.0 ** (-(np.maximum(levels, 2) - 2))
+    w[0] = 0.0
+    w *= (1.0 - ref_fraction) * n_total / w.sum()
+    w = np.maximum(w, 1.0)
+    pops = np.round(w * 65536.0).astype(np.int64)
+    signs = np.where(rng.random(n) < 0.5, -1, 1)
+    pops = pops * signs
+    pops[0] = int(round(ref_fraction * n_total * 65536.0))
+    return pops

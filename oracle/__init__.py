@@ -124,7 +124,8 @@ def lib():
             "orc_sim_get_record": (None, [c_void_p, POINTER(Record)]),
             "orc_sim_set_state": (None, [c_void_p, c_uint64, c_double, c_int32, c_double]),
             "orc_sim_get_state": (None, [c_void_p, u64p, dp, i32p, dp]),
-            "orc_generator_closure": (c_int64, [c_void_p, c_int, c_int]),
+            "orc_sim_sample_range": (c_int, [c_void_p, c_int64, c_int64, c_int64, c_int64]),
+            "orc_generator_closure": (c_int64, [c_void_p, c_int, c_int, u64p, c_int64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -267,7 +268,14 @@ class System:
 
     def generator_closure(self, max_level: int, expand_top: bool = True) -> int:
         """Determinants reached from HF by repeated excitation-generator draws."""
-        return int(lib().orc_generator_closure(self._h, max_level, int(expand_top)))
+        return int(lib().orc_generator_closure(self._h, max_level, int(expand_top), None, 0))
+
+    def space_keys(self, max_level: int, expand_top: bool = True) -> np.ndarray:
+        """Sorted rank keys of every determinant reached by the closure."""
+        n = self.generator_closure(max_level, expand_top)
+        out = np.zeros(n, dtype=np.uint64)
+        lib().orc_generator_closure(self._h, max_level, int(expand_top), out.ctypes.data_as(POINTER(c_uint64)), n)
+        return out
 
     def key_bound(self) -> int:
         return int(lib().orc_key_bound(self._h))
@@ -353,6 +361,13 @@ class Sim:
         rc = lib().orc_sim_step(self._h, int(propagate_only))
         if rc:
             raise RuntimeError(f"oracle step failed ({rc})")
+        return self.record()
+
+    def sample_range(self, i_lo: int, i_hi: int, g_lo: int, g_hi: int) -> Record:
+        """Propagate only the visits [i_lo, i_hi) and samples [g_lo, g_hi)."""
+        rc = lib().orc_sim_sample_range(self._h, i_lo, i_hi, g_lo, g_hi)
+        if rc:
+            raise RuntimeError(f"oracle sample_range failed ({rc})")
         return self.record()
 
     def run(self, nsteps: int):

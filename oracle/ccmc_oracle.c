@@ -973,10 +973,25 @@ static int annihilate(orc_sim *m)
     return 0;
 }
 
+static int sim_step_range(orc_sim *m, int propagate_only, int64_t i_lo, int64_t i_hi, int64_t g_lo, int64_t g_hi);
+
 /* One time step.  With propagate_only the spawned records and the death
  * deltas are produced but not annihilated and the iteration does not advance
  * (used to check the mean of one step against the exact action). */
 int orc_sim_step(orc_sim *m, int propagate_only)
+{
+    return sim_step_range(m, propagate_only, 0, INT64_MAX, 0, INT64_MAX);
+}
+
+/* Propagation (no annihilation) restricted to the non-composite visits
+ * [i_lo, i_hi) and the cluster samples [g_lo, g_hi) of the current step: the
+ * same per-sample work as a full step, for timing bounded samples of it. */
+int orc_sim_sample_range(orc_sim *m, int64_t i_lo, int64_t i_hi, int64_t g_lo, int64_t g_hi)
+{
+    return sim_step_range(m, 1, i_lo, i_hi, g_lo, g_hi);
+}
+
+static int sim_step_range(orc_sim *m, int propagate_only, int64_t i_lo, int64_t i_hi, int64_t g_lo, int64_t g_hi)
 {
     const orc_system *s = m->sys;
     int64_t n = m->n;
@@ -1029,10 +1044,14 @@ int orc_sim_step(orc_sim *m, int propagate_only)
     }
     int rc = 0;
     if (m->prm.fnc) {
-        m->rec.n_visit = n;
-        for (int64_t i = 0; i < n && !rc; i++) rc = visit_excitor(m, i);
+        int64_t hi = i_hi < n ? i_hi : n;
+        m->rec.n_visit = hi > i_lo ? hi - i_lo : 0;
+        for (int64_t i = i_lo; i < hi && !rc; i++) rc = visit_excitor(m, i);
     }
-    for (int64_t g = 0; g < n_sel && !rc; g++) rc = sample_cluster(m, (uint64_t)g, prefix, nex, mag, m->prm.fnc);
+    {
+        int64_t hi = g_hi < n_sel ? g_hi : n_sel;
+        for (int64_t g = g_lo; g < hi && !rc; g++) rc = sample_cluster(m, (uint64_t)g, prefix, nex, mag, m->prm.fnc);
+    }
     free(prefix);
     if (rc) return rc;
     m->rec.n_spawned = m->nsp;
@@ -1237,7 +1256,7 @@ static uint64_t r_for_index(uint64_t idx, uint64_t n)
     return (uint64_t)(num / n);
 }
 
-int64_t orc_generator_closure(const orc_system *s, int max_level, int expand_top)
+int64_t orc_generator_closure(const orc_system *s, int max_level, int expand_top, uint64_t *keys_out, int64_t cap)
 {
     uint64_t bound = s->nvranks * s->cocc;
     if (bound > (1ULL << 34)) return -1;
@@ -1290,6 +1309,12 @@ int64_t orc_generator_closure(const orc_system *s, int max_level, int expand_top
                 }
             }
         }
+    }
+    if (keys_out) {
+        /* keys in increasing order (bit-string order) */
+        int64_t m = 0;
+        for (uint64_t k = 0; k < bound && m < cap; k++)
+            if (seen[k >> 3] & (1u << (k & 7))) keys_out[m++] = k;
     }
     free(seen);
     free(queue);

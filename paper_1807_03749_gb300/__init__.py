@@ -1,0 +1,8 @@
+"""GB300-native coupled cluster Monte Carlo time step.
+
+The computation lives in the CUDA library built from ``csrc/`` (C ABI in
+``include/ccmc.h``); ``ccmc`` is its ctypes binding.
+"""
+from .ccmc import CCMCError, Context, from_workload, load  # noqa: F401
+
+__all__ = ["CCMCError", "Context", "from_workload", "load"]

@@ -1,0 +1,821 @@
+// ccmc_api.cu -- host side of the C ABI declared in include/ccmc.h.
+//
+// Builds the Hamiltonian tables (uniform electron gas: plane waves sorted by
+// |n|^2 then lexicographically, kinetic |k|^2/2, Coulomb 1/(pi L |n_q|^2);
+// generic: dense h1 and (pq|rs)), the rank-key tables, allocates the device
+// state and sequences the kernels of ccmc_step.cu.  The host evaluates only
+// the logarithm of the shift update (Sec. II: the shift is held, then varied
+// to keep the population stable) every shift_a steps.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ccmc.h"
+#include "ccmc_state.cuh"
+
+using namespace ccmc;
+
+namespace {
+
+constexpr double PI_D = 3.14159265358979323846;
+
+struct HostSys {
+    int kind = 0, nel = 0, nso = 0, lmax = 0, nw = 0;
+    double rs = 0.0, L = 0.0, ecore = 0.0;
+    int npw = 0, nmax = 0, side = 0;
+    std::vector<int> kv, grid;
+    std::vector<double> tkin, vtab, h1, eri;
+    int norb = 0;
+    std::vector<u64> rank_tab;
+    u64 cocc = 0, nvranks = 0;
+    u64 binom[RANK_STRIDE][8];
+    double ehf_rel = 0.0;
+    u64 npairs = 0, nvirt = 0, ns = 0, nd = 0, ndcase[3] = {0, 0, 0};
+    int no[2] = {0, 0}, nv[2] = {0, 0};
+    double inv_pgen_ueg = 0.0, inv_pgen_single[2] = {0, 0}, inv_pgen_double[3] = {0, 0, 0};
+};
+
+void fill_binom(HostSys &h)
+{
+    for (int n = 0; n < RANK_STRIDE; n++)
+        for (int k = 0; k < 8; k++)
+            h.binom[n][k] = k == 0 ? 1 : (n == 0 ? 0 : h.binom[n - 1][k - 1] + h.binom[n - 1][k]);
+}
+
+// <D|H|D> without core energy, same operation order as the device code
+double host_diag(const HostSys &h, const std::vector<int> &occ)
+{
+    const int n = (int)occ.size();
+    if (h.kind == CCMC_UEG) {
+        double tsum = 0.0, xsum = 0.0;
+        for (int i = 0; i < n; i++) tsum = tsum + h.tkin[occ[i]];
+        for (int i = 0; i < n; i++)
+            for (int j = i + 1; j < n; j++)
+                if (((occ[i] ^ occ[j]) & 1) == 0) {
+                    const int *a = &h.kv[3 * (occ[i] >> 1)], *b = &h.kv[3 * (occ[j] >> 1)];
+                    int dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+                    xsum = xsum + h.vtab[dx * dx + dy * dy + dz * dz];
+                }
+        return tsum - xsum;
+    }
+    double e1 = 0.0, e2 = 0.0;
+    const size_t no = (size_t)h.norb;
+    for (int i = 0; i < n; i++) {
+        int P = occ[i] >> 1;
+        e1 = e1 + h.h1[P * no + P];
+    }
+    for (int i = 0; i < n; i++)
+        for (int j = i + 1; j < n; j++) {
+            size_t P = occ[i] >> 1, Q = occ[j] >> 1;
+            double t = h.eri[((P * no + P) * no + Q) * no + Q];
+            if (((occ[i] ^ occ[j]) & 1) == 0) t = t - h.eri[((P * no + Q) * no + Q) * no + P];
+            e2 = e2 + t;
+        }
+    return e1 + e2;
+}
+
+bool build_ueg(HostSys &h)
+{
+    h.npw = h.nso / 2;
+    // plane waves with |n|^2 <= ecut; the smallest ecut whose count is npw
+    int ecut = -1;
+    for (int e = 0; e < 100; e++) {
+        int r = (int)std::ceil(std::sqrt((double)e)) + 1, c = 0;
+        for (int x = -r; x <= r; x++)
+            for (int y = -r; y <= r; y++)
+                for (int z = -r; z <= r; z++)
+                    if (x * x + y * y + z * z <= e) c++;
+        if (c == h.npw) { ecut = e; break; }
+        if (c > h.npw) break;
+    }
+    if (ecut < 0) return false;
+    std::vector<std::array<int, 3>> v;
+    int r = (int)std::ceil(std::sqrt((double)ecut)) + 1;
+    for (int x = -r; x <= r; x++)
+        for (int y = -r; y <= r; y++)
+            for (int z = -r; z <= r; z++)
+                if (x * x + y * y + z * z <= ecut) v.push_back({x, y, z});
+    std::sort(v.begin(), v.end(), [](const std::array<int, 3> &a, const std::array<int, 3> &b) {
+        int na = a[0] * a[0] + a[1] * a[1] + a[2] * a[2], nb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+        if (na != nb) return na < nb;
+        return a < b;
+    });
+    h.kv.resize(3 * h.npw);
+    h.nmax = 0;
+    for (int i = 0; i < h.npw; i++)
+        for (int c = 0; c < 3; c++) {
+            h.kv[3 * i + c] = v[i][c];
+            h.nmax = std::max(h.nmax, std::abs(v[i][c]));
+        }
+    h.side = 2 * h.nmax + 1;
+    h.grid.assign((size_t)h.side * h.side * h.side, -1);
+    for (int i = 0; i < h.npw; i++)
+        h.grid[((h.kv[3 * i] + h.nmax) * h.side + (h.kv[3 * i + 1] + h.nmax)) * h.side + (h.kv[3 * i + 2] + h.nmax)] = i;
+    h.L = h.rs * std::cbrt((4.0 * PI_D * (double)h.nel) / 3.0);
+    h.tkin.resize(h.nso);
+    for (int p = 0; p < h.nso; p++) {
+        const int *k = &h.kv[3 * (p >> 1)];
+        int n2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        h.tkin[p] = ((2.0 * PI_D * PI_D) * (double)n2) / (h.L * h.L);
+    }
+    int n2tab = 12 * h.nmax * h.nmax + 1;
+    h.vtab.assign(n2tab, 0.0);
+    for (int n2 = 1; n2 < n2tab; n2++) h.vtab[n2] = 1.0 / ((PI_D * h.L) * (double)n2);
+    return true;
+}
+
+struct Alloc {
+    ccmc_alloc_fn fa = nullptr;
+    ccmc_free_fn ff = nullptr;
+    void *user = nullptr;
+    std::vector<void *> blocks;
+    bool failed = false;
+
+    void *get(size_t bytes)
+    {
+        if (bytes == 0) bytes = 256;
+        bytes = (bytes + 255) & ~(size_t)255;
+        void *p = nullptr;
+        if (fa) p = fa(bytes, user);
+        else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+        if (!p) { failed = true; return nullptr; }
+        blocks.push_back(p);
+        return p;
+    }
+    template <typename T>
+    T *arr(size_t n) { return (T *)get(n * sizeof(T)); }
+    void release()
+    {
+        for (void *p : blocks) {
+            if (ff) ff(p, user);
+            else if (!fa) cudaFree(p);
+        }
+        blocks.clear();
+    }
+};
+
+}  // namespace
+
+struct ccmc_ctx {
+    HostSys hs;
+    StepCtx sc;
+    Alloc al;
+    ccmc_params prm;
+    cudaStream_t stream = nullptr;
+    // host mirror of the shift state
+    u64 iter = 0;
+    double shift = 0.0;
+    int vary = 0;
+    double nprev = 0.0;
+    u64 records_read = 0;
+    bool stepped = false;
+    // pinned staging
+    DevStep *h_st = nullptr;
+    double *h_shift = nullptr;
+    std::string err;
+    i64 list_cap = 0, spawn_cap = 0, cl_cap = 0;
+    double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    i64 phase_launch0[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+ccmc_status fail(ccmc_ctx *c, ccmc_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+ccmc_status cuda_fail(ccmc_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, CCMC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+    } while (0)
+
+ccmc_status status_from_bits(ccmc_ctx *ctx, unsigned bits)
+{
+    if (bits & ERRB_SPAWN_OVERFLOW) return fail(ctx, CCMC_ERR_SPAWN_OVERFLOW, "spawned particles exceeded spawn_capacity");
+    if (bits & ERRB_CLUSTER_OVERFLOW) return fail(ctx, CCMC_ERR_SPAWN_OVERFLOW, "multi-spawn clusters exceeded capacity");
+    if (bits & ERRB_LIST_OVERFLOW) return fail(ctx, CCMC_ERR_LIST_OVERFLOW, "occupied excitors exceeded list_capacity");
+    if (bits & ERRB_NUMERIC) return fail(ctx, CCMC_ERR_NUMERIC, "a weight left the fixed-point range");
+    return CCMC_OK;
+}
+
+// device helper kernels for list upload: keys and diagonal energies
+template <int K>
+__global__ void k_prepare_list(SysDev s, ListView L, i64 n)
+{
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+        Det<K> d;
+        for (int w = 0; w < K; w++) d.w[w] = L.bits[w * L.cap + i];
+        L.key[i] = rank_key(s, d);
+        L.diag[i] = is_hf(s, d) ? 0.0 : diag_rel(s, d);
+    }
+}
+
+cudaError_t prepare_list(ccmc_ctx *ctx, ListView &L, i64 n)
+{
+    int g = (int)std::min<i64>(4096, (n + 255) / 256 + 1);
+    switch (ctx->sc.K) {
+    case 1: k_prepare_list<1><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n); break;
+    case 2: k_prepare_list<2><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n); break;
+    default: k_prepare_list<3><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, int truncation_level,
+                      const ccmc_params *params, ccmc_ctx **out)
+{
+    if (!out) return CCMC_ERR_ARG;
+    *out = nullptr;
+    if (!ham || !params) return CCMC_ERR_ARG;
+    const int nel = ham->n_electrons, nso = ham->n_spinorb, l = truncation_level;
+    if (nel < 2 || nso <= nel || nso > 64 * MAXK || (nso & 1) || l < 1 || l > 4) return CCMC_ERR_ARG;
+    if (ham->kind != CCMC_UEG && ham->kind != CCMC_GENERIC) return CCMC_ERR_ARG;
+    if (ham->kind == CCMC_GENERIC && (!ham->h1 || !ham->eri)) return CCMC_ERR_ARG;
+    if (!(params->tau > 0.0) || params->shift_a < 1 || !(params->d0_init > 0.0)) return CCMC_ERR_ARG;
+    if (params->multispawn && !(params->a_thresh > 0.0)) return CCMC_ERR_ARG;
+    if (params->radix_bits < 0 || params->radix_bits > MAX_DIGIT_BITS) return CCMC_ERR_ARG;
+
+    ccmc_ctx *ctx = new (std::nothrow) ccmc_ctx();
+    if (!ctx) return CCMC_ERR_OOM;
+    ctx->prm = *params;
+    HostSys &h = ctx->hs;
+    h.kind = ham->kind;
+    h.nel = nel;
+    h.nso = nso;
+    h.lmax = l;
+    h.nw = (nso + 63) / 64;
+    h.rs = ham->rs;
+    h.ecore = ham->kind == CCMC_GENERIC ? ham->e_core : 0.0;
+    // the reference must be the lowest N spin-orbitals
+    if (ref && ref->bits) {
+        for (int w = 0; w < h.nw; w++) {
+            u64 want = 0;
+            for (int p = 64 * w; p < std::min(64 * w + 64, nel); p++) want |= 1ULL << (p & 63);
+            if (ref->bits[w] != want) { delete ctx; return CCMC_ERR_ARG; }
+        }
+    }
+    if (h.kind == CCMC_UEG) {
+        if (!(h.rs > 0.0) || !build_ueg(h)) { delete ctx; return CCMC_ERR_ARG; }
+    } else {
+        h.norb = nso / 2;
+        size_t n2 = (size_t)h.norb * h.norb;
+        h.h1.assign(ham->h1, ham->h1 + n2);
+        h.eri.assign(ham->eri, ham->eri + n2 * n2);
+    }
+    fill_binom(h);
+    // rank tables
+    h.rank_tab.assign((size_t)(l + 1) * RANK_STRIDE, 0);
+    for (int c = 0; c <= l; c++)
+        for (int q = 0; q < RANK_STRIDE; q++) {
+            u64 s = 0;
+            for (int j = 0; j <= l - c; j++) s += h.binom[q][j];
+            h.rank_tab[(size_t)c * RANK_STRIDE + q] = s;
+        }
+    h.cocc = h.rank_tab[nel];                        // c = 0 row at q = N
+    h.nvranks = h.rank_tab[nso - nel];
+    // reference energy and generator constants
+    std::vector<int> hfocc(nel);
+    for (int p = 0; p < nel; p++) hfocc[p] = p;
+    h.ehf_rel = host_diag(h, hfocc);
+    h.npairs = (u64)nel * (u64)(nel - 1) / 2;
+    h.nvirt = (u64)(nso - nel);
+    if (h.kind == CCMC_UEG) {
+        h.inv_pgen_ueg = (double)(h.npairs * h.nvirt) * 0.5;
+    } else {
+        for (int p = 0; p < nel; p++) h.no[p & 1]++;
+        h.nv[0] = h.norb - h.no[0];
+        h.nv[1] = h.norb - h.no[1];
+        h.ns = (u64)h.no[0] * h.nv[0] + (u64)h.no[1] * h.nv[1];
+        h.ndcase[0] = h.binom[h.nv[0]][2];
+        h.ndcase[1] = h.binom[h.nv[1]][2];
+        h.ndcase[2] = (u64)h.nv[0] * (u64)h.nv[1];
+        h.nd = h.binom[h.no[0]][2] * h.ndcase[0] + h.binom[h.no[1]][2] * h.ndcase[1] +
+               (u64)h.no[0] * h.no[1] * h.ndcase[2];
+        for (int sg = 0; sg < 2; sg++)
+            h.inv_pgen_single[sg] = ((double)((u64)nel * (u64)h.nv[sg]) * (double)(h.ns + h.nd)) / (double)h.ns;
+        for (int c = 0; c < 3; c++)
+            h.inv_pgen_double[c] = ((double)(h.npairs * h.ndcase[c]) * (double)(h.ns + h.nd)) / (double)h.nd;
+    }
+
+    // capacities
+    double tgt = std::max(params->target_pop, params->d0_init);
+    u64 key_bound = h.nvranks * h.cocc;
+    ctx->list_cap = params->list_capacity ? (i64)params->list_capacity
+                                          : (i64)std::min<double>((double)key_bound, 2.0 * tgt + 4096.0);
+    ctx->spawn_cap = params->spawn_capacity ? (i64)params->spawn_capacity : (i64)(8.0 * tgt + 65536.0);
+    ctx->cl_cap = params->multispawn ? (i64)(3.0 * tgt + 65536.0) : 1;
+    if (ctx->list_cap < 2 || ctx->spawn_cap < 1 || ctx->spawn_cap >= (i64)0xFFFFFFFFLL) {
+        delete ctx;
+        return CCMC_ERR_ARG;
+    }
+
+    ctx->stream = (cudaStream_t)params->cuda_stream;
+    ctx->al.fa = params->alloc;
+    ctx->al.ff = params->free;
+    ctx->al.user = params->alloc_user;
+    Alloc &al = ctx->al;
+
+    // device tables
+    SysDev &s = ctx->sc.sys;
+    memset(&s, 0, sizeof(s));
+    s.kind = h.kind;
+    s.nel = nel;
+    s.nso = nso;
+    s.lmax = l;
+    s.nw = h.nw;
+    for (int w = 0; w < MAXK; w++) {
+        u64 hf = 0, valid = 0, virt = 0;
+        for (int b = 0; b < 64; b++) {
+            int p = 64 * w + b;
+            if (p < nel) hf |= 1ULL << b;
+            if (p < nso) valid |= 1ULL << b;
+            if (p >= nel && p < nso) virt |= 1ULL << b;
+        }
+        s.hf[w] = hf;
+        s.valid[w] = valid;
+        s.virt[w] = virt;
+    }
+    auto upload = [&](const void *src, size_t bytes) -> void * {
+        void *d = al.get(bytes);
+        if (d && bytes) cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice);
+        return d;
+    };
+    if (h.kind == CCMC_UEG) {
+        s.nmax = h.nmax;
+        s.side = h.side;
+        s.grid = (const int *)upload(h.grid.data(), h.grid.size() * sizeof(int));
+        s.kv = (const int *)upload(h.kv.data(), h.kv.size() * sizeof(int));
+        s.tkin = (const double *)upload(h.tkin.data(), h.tkin.size() * sizeof(double));
+        s.vtab = (const double *)upload(h.vtab.data(), h.vtab.size() * sizeof(double));
+        s.inv_pgen_ueg = h.inv_pgen_ueg;
+    } else {
+        s.norb = h.norb;
+        s.h1 = (const double *)upload(h.h1.data(), h.h1.size() * sizeof(double));
+        s.eri = (const double *)upload(h.eri.data(), h.eri.size() * sizeof(double));
+        s.nv[0] = h.nv[0];
+        s.nv[1] = h.nv[1];
+        s.ns = h.ns;
+        s.ns_nd = h.ns + h.nd;
+        for (int c = 0; c < 3; c++) {
+            s.ndcase[c] = h.ndcase[c];
+            s.inv_pgen_double[c] = h.inv_pgen_double[c];
+        }
+        s.inv_pgen_single[0] = h.inv_pgen_single[0];
+        s.inv_pgen_single[1] = h.inv_pgen_single[1];
+    }
+    s.npairs = h.npairs;
+    s.nvirt = h.nvirt;
+    s.rank_tab = (const u64 *)upload(h.rank_tab.data(), h.rank_tab.size() * sizeof(u64));
+    s.cocc = h.cocc;
+    s.ehf_rel = h.ehf_rel;
+
+    RunParams &rp = ctx->sc.prm;
+    rp.tau = params->tau;
+    rp.spawn_cutoff = params->spawn_cutoff;
+    rp.a_thresh = params->a_thresh;
+    rp.seed = params->seed;
+    rp.replica = params->replica;
+    rp.fnc = params->fnc ? 1 : 0;
+    rp.multispawn = params->multispawn ? 1 : 0;
+
+    // shapes
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    Shapes &sh = ctx->sc.sh;
+    sh.scan_grid = std::min(1024, 2 * nsm);
+    sh.work_grid = 8 * nsm;
+    sh.sort_grid = 2 * nsm;
+    sh.key_bits = bits_for(key_bound);
+    sh.digit_bits = params->radix_bits ? params->radix_bits : MAX_DIGIT_BITS;
+    sh.enum_slots = sh.scan_grid + sh.work_grid;
+    ctx->sc.K = h.nw;
+
+    // lists
+    const int K = h.nw;
+    for (int b = 0; b < 2; b++) {
+        ListView &L = ctx->sc.list[b];
+        L.cap = ctx->list_cap;
+        L.bits = al.arr<u64>((size_t)K * L.cap);
+        L.key = al.arr<u64>(L.cap);
+        L.pop = al.arr<i64>(L.cap);
+        L.diag = al.arr<double>(L.cap);
+    }
+    SpawnBuf &sp = ctx->sc.sp;
+    sp.cap = ctx->spawn_cap;
+    for (int b = 0; b < 2; b++) {
+        sp.key[b] = al.arr<u64>(sp.cap);
+        sp.pop[b] = al.arr<i64>(sp.cap);
+    }
+    ClusterBuf &cl = ctx->sc.cl;
+    cl.cap = ctx->cl_cap;
+    cl.bits = al.arr<u64>((size_t)K * cl.cap);
+    cl.catt = al.arr<double>(cl.cap);
+    cl.index = al.arr<u64>(cl.cap);
+    cl.end = al.arr<i64>(cl.cap);
+    WorkArrays &wa = ctx->sc.wa;
+    const i64 lc = ctx->list_cap;
+    wa.prefix = al.arr<i64>(lc);
+    wa.att_end = al.arr<i64>(lc);
+    wa.catt = al.arr<double>(lc);
+    wa.death = al.arr<i64>(lc);
+    wa.acc = al.arr<i64>(lc);
+    wa.newpop = al.arr<i64>(lc);
+    wa.keep_l = al.arr<i64>(lc);
+    wa.keep_s = al.arr<i64>(sp.cap);
+    wa.ins = al.arr<i64>(sp.cap);
+    wa.part = al.arr<i64>(4 * 2 * (size_t)std::max(sh.scan_grid, sh.work_grid));
+    wa.enum_part = al.arr<double>(2 * (size_t)sh.enum_slots);
+    wa.hist = al.arr<unsigned>((size_t)(1 << MAX_DIGIT_BITS) * sh.sort_grid);
+    wa.ring = al.arr<Record>(RING);
+    ctx->sc.st = al.arr<DevStep>(1);
+    if (al.failed) {
+        al.release();
+        delete ctx;
+        return CCMC_ERR_OOM;
+    }
+    if (cudaMallocHost(&ctx->h_st, sizeof(DevStep)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_shift, sizeof(double)) != cudaSuccess) {
+        al.release();
+        delete ctx;
+        return CCMC_ERR_OOM;
+    }
+    ctx->sc.stream = ctx->stream;
+    ctx->sc.cur = 0;
+    ctx->sc.sorted_buf = 0;
+    ctx->sc.profile = false;
+    for (int e = 0; e < 8; e++) {
+        ctx->sc.launches[e] = 0;
+        if (cudaEventCreate(&ctx->sc.events[e]) != cudaSuccess) {
+            al.release();
+            delete ctx;
+            return CCMC_ERR_CUDA;
+        }
+    }
+
+    // initial state: d0_init on HF
+    ctx->iter = 0;
+    ctx->shift = 0.0;
+    ctx->vary = 0;
+    ctx->nprev = params->d0_init;
+    std::vector<uint64_t> hfw(K);
+    for (int w = 0; w < K; w++) hfw[w] = s.hf[w];
+    int64_t pop0 = (int64_t)std::llround(params->d0_init * 65536.0);
+    ccmc_status st = ccmc_set_list(ctx, hfw.data(), &pop0, 1);
+    if (st != CCMC_OK) {
+        ccmc_free(ctx);
+        return st;
+    }
+    *out = ctx;
+    return CCMC_OK;
+}
+
+ccmc_status ccmc_set_list(ccmc_ctx *ctx, const uint64_t *bits, const int64_t *pop, size_t n)
+{
+    if (!ctx || !bits || !pop || n < 1) return fail(ctx, CCMC_ERR_ARG, "empty list");
+    if ((i64)n > ctx->list_cap) return fail(ctx, CCMC_ERR_LIST_OVERFLOW, "list larger than list_capacity");
+    const HostSys &h = ctx->hs;
+    const int K = h.nw;
+    // validate: popcount N, level <= l, first entry HF
+    for (size_t i = 0; i < n; i++) {
+        int pc = 0, holes = 0;
+        for (int w = 0; w < K; w++) {
+            pc += __builtin_popcountll(bits[i * K + w]);
+            holes += __builtin_popcountll(ctx->sc.sys.hf[w] & ~bits[i * K + w]);
+            if (bits[i * K + w] & ~ctx->sc.sys.valid[w]) return fail(ctx, CCMC_ERR_ARG, "orbital beyond M");
+        }
+        if (pc != h.nel) return fail(ctx, CCMC_ERR_ARG, "wrong electron count");
+        if (holes > h.lmax) return fail(ctx, CCMC_ERR_ARG, "excitor beyond the truncation level");
+        if (i == 0 && holes != 0) return fail(ctx, CCMC_ERR_ARG, "first entry must be HF");
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    ListView &L = ctx->sc.list[ctx->sc.cur];
+    std::vector<u64> soa((size_t)K * n);
+    for (size_t i = 0; i < n; i++)
+        for (int w = 0; w < K; w++) soa[(size_t)w * n + i] = bits[i * K + w];
+    for (int w = 0; w < K; w++)
+        CK(cudaMemcpy(L.bits + (size_t)w * L.cap, soa.data() + (size_t)w * n, n * sizeof(u64), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.pop, pop, n * sizeof(i64), cudaMemcpyHostToDevice));
+    CK(prepare_list(ctx, L, (i64)n));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::vector<u64> keys(n);
+    CK(cudaMemcpy(keys.data(), L.key, n * sizeof(u64), cudaMemcpyDeviceToHost));
+    for (size_t i = 1; i < n; i++)
+        if (keys[i] <= keys[i - 1]) return fail(ctx, CCMC_ERR_ARG, "list not sorted and unique");
+    DevStep st;
+    memset(&st, 0, sizeof(st));
+    st.iter = ctx->iter;
+    st.shift = ctx->shift;
+    st.n_occ = (i64)n;
+    CK(cudaMemcpy(ctx->sc.st, &st, sizeof(DevStep), cudaMemcpyHostToDevice));
+    ctx->stepped = false;
+    return CCMC_OK;
+}
+
+static ccmc_status check_device(ccmc_ctx *ctx)
+{
+    CK(cudaMemcpyAsync(ctx->h_st, ctx->sc.st, sizeof(DevStep), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return status_from_bits(ctx, ctx->h_st->err);
+}
+
+ccmc_status ccmc_step(ccmc_ctx *ctx, int nsteps)
+{
+    if (!ctx || nsteps < 0) return CCMC_ERR_ARG;
+    const int A = ctx->prm.shift_a;
+    for (int k = 0; k < nsteps; k++) {
+        cudaError_t e = launch_step(ctx->sc);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "launch_step");
+        ctx->stepped = true;
+        if (ctx->sc.profile) {
+            CK(cudaEventSynchronize(ctx->sc.events[NPHASES]));
+            for (int ph = 0; ph < NPHASES; ph++) {
+                float ms = 0.0f;
+                CK(cudaEventElapsedTime(&ms, ctx->sc.events[ph], ctx->sc.events[ph + 1]));
+                ctx->phase_ms[ph] += ms;
+            }
+        }
+        u64 it = ctx->iter;
+        ctx->iter++;
+        if ((it + 1) % (u64)A == 0) {
+            ccmc_status s = check_device(ctx);
+            if (s != CCMC_OK) return s;
+            Record r;
+            CK(cudaMemcpy(&r, ctx->sc.wa.ring + (it % RING), sizeof(Record), cudaMemcpyDeviceToHost));
+            double nt = (double)r.ntot_after / 65536.0;
+            double prev = ctx->shift;
+            if (ctx->vary && nt > 0.0 && ctx->nprev > 0.0)
+                ctx->shift = ctx->shift - (ctx->prm.zeta / ((double)A * ctx->prm.tau)) * std::log(nt / ctx->nprev);
+            if (!ctx->vary && nt > ctx->prm.target_pop) ctx->vary = 1;
+            ctx->nprev = nt;
+            if (ctx->shift != prev) {
+                *ctx->h_shift = ctx->shift;
+                CK(cudaMemcpyAsync(&ctx->sc.st->shift, ctx->h_shift, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+                CK(cudaStreamSynchronize(ctx->stream));
+            }
+        }
+    }
+    return CCMC_OK;
+}
+
+ccmc_status ccmc_profile(ccmc_ctx *ctx, int32_t enable)
+{
+    if (!ctx) return CCMC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->sc.profile = enable != 0;
+    for (int ph = 0; ph < 8; ph++) {
+        ctx->phase_ms[ph] = 0.0;
+        ctx->phase_launch0[ph] = ctx->sc.launches[ph];
+    }
+    return CCMC_OK;
+}
+
+ccmc_status ccmc_phase_times(ccmc_ctx *ctx, double *ms, int64_t *launches, int32_t nphases, int64_t *total_launches)
+{
+    if (!ctx || nphases < 0) return CCMC_ERR_ARG;
+    for (int ph = 0; ph < nphases && ph < NPHASES; ph++) {
+        if (ms) ms[ph] = ctx->phase_ms[ph];
+        if (launches) launches[ph] = ctx->sc.launches[ph] - ctx->phase_launch0[ph];
+    }
+    if (total_launches) {
+        i64 t = 0;
+        for (int ph = 0; ph < NPHASES; ph++) t += ctx->sc.launches[ph];
+        *total_launches = t;
+    }
+    return CCMC_OK;
+}
+
+ccmc_status ccmc_sync(ccmc_ctx *ctx)
+{
+    if (!ctx) return CCMC_ERR_ARG;
+    return check_device(ctx);
+}
+
+ccmc_status ccmc_energy(ccmc_ctx *ctx, double *e_proj, double *e_num, double *n0, double *shift, double *n_total)
+{
+    if (!ctx) return CCMC_ERR_ARG;
+    ccmc_status s = check_device(ctx);
+    if (s != CCMC_OK) return s;
+    if (!ctx->stepped && ctx->iter == 0) {
+        if (e_proj) *e_proj = 0.0;
+        if (e_num) *e_num = 0.0;
+        if (n0) *n0 = ctx->prm.d0_init;
+        if (shift) *shift = ctx->shift;
+        if (n_total) *n_total = ctx->prm.d0_init;
+        return CCMC_OK;
+    }
+    Record r;
+    CK(cudaMemcpy(&r, ctx->sc.wa.ring + ((ctx->iter - 1) % RING), sizeof(Record), cudaMemcpyDeviceToHost));
+    double n0d = (double)r.n0 / 65536.0;
+    if (e_proj) *e_proj = n0d != 0.0 ? r.e_num / n0d : 0.0;
+    if (e_num) *e_num = r.e_num;
+    if (n0) *n0 = n0d;
+    if (shift) *shift = r.shift;
+    if (n_total) *n_total = (double)r.ntot_after / 65536.0;
+    return CCMC_OK;
+}
+
+ccmc_status ccmc_reference_energy(ccmc_ctx *ctx, double *e_hf)
+{
+    if (!ctx || !e_hf) return CCMC_ERR_ARG;
+    *e_hf = ctx->hs.ehf_rel + ctx->hs.ecore;
+    return CCMC_OK;
+}
+
+ccmc_status ccmc_get_records(ccmc_ctx *ctx, ccmc_record *out, size_t cap, size_t *n)
+{
+    if (!ctx || !n) return CCMC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    u64 first = ctx->records_read;
+    if (ctx->iter > (u64)RING && first < ctx->iter - RING) first = ctx->iter - RING;
+    u64 count = ctx->iter - first;
+    if (count > cap) {
+        first = ctx->iter - cap;
+        count = cap;
+    }
+    static_assert(sizeof(Record) == sizeof(ccmc_record), "record layout");
+    for (u64 k = 0; k < count; k++)
+        CK(cudaMemcpy(out + k, ctx->sc.wa.ring + ((first + k) % RING), sizeof(Record), cudaMemcpyDeviceToHost));
+    ctx->records_read = ctx->iter;
+    *n = (size_t)count;
+    return CCMC_OK;
+}
+
+ccmc_status ccmc_list_size(ccmc_ctx *ctx, size_t *n)
+{
+    if (!ctx || !n) return CCMC_ERR_ARG;
+    ccmc_status s = check_device(ctx);
+    if (s != CCMC_OK) return s;
+    *n = (size_t)ctx->h_st->n_occ;
+    return CCMC_OK;
+}
+
+ccmc_status ccmc_get_list(ccmc_ctx *ctx, uint64_t *bits, uint64_t *keys, int64_t *pop, size_t cap, size_t *n)
+{
+    size_t m = 0;
+    ccmc_status s = ccmc_list_size(ctx, &m);
+    if (s != CCMC_OK) return s;
+    if (n) *n = m;
+    if (m > cap) return fail(ctx, CCMC_ERR_ARG, "buffer too small");
+    const ListView &L = ctx->sc.list[ctx->sc.cur];
+    const int K = ctx->hs.nw;
+    if (bits) {
+        std::vector<u64> soa((size_t)K * m);
+        for (int w = 0; w < K; w++)
+            CK(cudaMemcpy(soa.data() + (size_t)w * m, L.bits + (size_t)w * L.cap, m * sizeof(u64), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < m; i++)
+            for (int w = 0; w < K; w++) bits[i * K + w] = soa[(size_t)w * m + i];
+    }
+    if (keys) CK(cudaMemcpy(keys, L.key, m * sizeof(u64), cudaMemcpyDeviceToHost));
+    if (pop) CK(cudaMemcpy(pop, L.pop, m * sizeof(i64), cudaMemcpyDeviceToHost));
+    return CCMC_OK;
+}
+
+ccmc_status ccmc_get_spawned(ccmc_ctx *ctx, uint64_t *keys, int64_t *pop, size_t cap, size_t *n)
+{
+    if (!ctx || !n) return CCMC_ERR_ARG;
+    ccmc_status s = check_device(ctx);
+    if (s != CCMC_OK) return s;
+    if (!ctx->stepped) {
+        *n = 0;
+        return CCMC_OK;
+    }
+    i64 m = std::min<i64>(ctx->h_st->n_sp, ctx->spawn_cap);
+    *n = (size_t)m;
+    if ((size_t)m > cap) return fail(ctx, CCMC_ERR_ARG, "buffer too small");
+    if (keys) CK(cudaMemcpy(keys, ctx->sc.sp.key[ctx->sc.sorted_buf], m * sizeof(u64), cudaMemcpyDeviceToHost));
+    if (pop) CK(cudaMemcpy(pop, ctx->sc.sp.pop[ctx->sc.sorted_buf], m * sizeof(i64), cudaMemcpyDeviceToHost));
+    return CCMC_OK;
+}
+
+ccmc_status ccmc_get_death(ccmc_ctx *ctx, int64_t *death, size_t cap, size_t *n)
+{
+    if (!ctx || !n) return CCMC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (!ctx->stepped) {
+        *n = 0;
+        return CCMC_OK;
+    }
+    // the death deltas belong to the list at the start of the latest step
+    CK(cudaMemcpy(ctx->h_st, ctx->sc.st, sizeof(DevStep), cudaMemcpyDeviceToHost));
+    size_t m = (size_t)ctx->h_st->n_start;
+    *n = m;
+    if (m > cap) return fail(ctx, CCMC_ERR_ARG, "buffer too small");
+    if (death) CK(cudaMemcpy(death, ctx->sc.wa.death, m * sizeof(i64), cudaMemcpyDeviceToHost));
+    return CCMC_OK;
+}
+
+ccmc_status ccmc_set_state(ccmc_ctx *ctx, uint64_t iter, double shift, int32_t vary, double nprev)
+{
+    if (!ctx) return CCMC_ERR_ARG;
+    ctx->iter = iter;
+    ctx->shift = shift;
+    ctx->vary = vary ? 1 : 0;
+    ctx->nprev = nprev;
+    ctx->records_read = iter;
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(&ctx->sc.st->iter, &iter, sizeof(u64), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(&ctx->sc.st->shift, &shift, sizeof(double), cudaMemcpyHostToDevice));
+    return CCMC_OK;
+}
+
+ccmc_status ccmc_get_state(ccmc_ctx *ctx, uint64_t *iter, double *shift, int32_t *vary, double *nprev)
+{
+    if (!ctx) return CCMC_ERR_ARG;
+    if (iter) *iter = ctx->iter;
+    if (shift) *shift = ctx->shift;
+    if (vary) *vary = ctx->vary;
+    if (nprev) *nprev = ctx->nprev;
+    return CCMC_OK;
+}
+
+ccmc_status ccmc_save(ccmc_ctx *ctx, const char *path)
+{
+    if (!ctx || !path) return CCMC_ERR_ARG;
+    size_t n = 0;
+    ccmc_status s = ccmc_list_size(ctx, &n);
+    if (s != CCMC_OK) return s;
+    const int K = ctx->hs.nw;
+    std::vector<uint64_t> bits((size_t)K * n);
+    std::vector<int64_t> pop(n);
+    s = ccmc_get_list(ctx, bits.data(), nullptr, pop.data(), n, &n);
+    if (s != CCMC_OK) return s;
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(ctx, CCMC_ERR_ARG, "cannot open checkpoint for writing");
+    const char magic[8] = {'C', 'C', 'M', 'C', 'C', 'K', '0', '1'};
+    int32_t hdr[4] = {ctx->hs.nel, ctx->hs.nso, ctx->hs.lmax, K};
+    u64 nn = n;
+    bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+              fwrite(&ctx->iter, 8, 1, f) == 1 && fwrite(&ctx->shift, 8, 1, f) == 1 &&
+              fwrite(&ctx->vary, 4, 1, f) == 1 && fwrite(&ctx->nprev, 8, 1, f) == 1 && fwrite(&nn, 8, 1, f) == 1 &&
+              fwrite(bits.data(), 8, bits.size(), f) == bits.size() && fwrite(pop.data(), 8, n, f) == n;
+    fclose(f);
+    return ok ? CCMC_OK : fail(ctx, CCMC_ERR_ARG, "checkpoint write failed");
+}
+
+ccmc_status ccmc_load(ccmc_ctx *ctx, const char *path)
+{
+    if (!ctx || !path) return CCMC_ERR_ARG;
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(ctx, CCMC_ERR_ARG, "cannot open checkpoint");
+    char magic[8];
+    int32_t hdr[4];
+    u64 iter, nn;
+    double shift, nprev;
+    int32_t vary;
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "CCMCCK01", 8) == 0 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
+              fread(&iter, 8, 1, f) == 1 && fread(&shift, 8, 1, f) == 1 && fread(&vary, 4, 1, f) == 1 &&
+              fread(&nprev, 8, 1, f) == 1 && fread(&nn, 8, 1, f) == 1;
+    if (!ok || hdr[0] != ctx->hs.nel || hdr[1] != ctx->hs.nso || hdr[2] != ctx->hs.lmax || hdr[3] != ctx->hs.nw ||
+        nn < 1 || nn > (u64)ctx->list_cap) {
+        fclose(f);
+        return fail(ctx, CCMC_ERR_ARG, "checkpoint does not match this context");
+    }
+    const int K = ctx->hs.nw;
+    std::vector<uint64_t> bits((size_t)K * nn);
+    std::vector<int64_t> pop(nn);
+    ok = fread(bits.data(), 8, bits.size(), f) == bits.size() && fread(pop.data(), 8, nn, f) == nn;
+    fclose(f);
+    if (!ok) return fail(ctx, CCMC_ERR_ARG, "truncated checkpoint");
+    ccmc_status s = ccmc_set_state(ctx, iter, shift, vary, nprev);
+    if (s != CCMC_OK) return s;
+    return ccmc_set_list(ctx, bits.data(), pop.data(), nn);
+}
+
+const char *ccmc_last_error(ccmc_ctx *ctx)
+{
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+void ccmc_free(ccmc_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    ctx->al.release();
+    for (int e = 0; e < 8; e++)
+        if (ctx->sc.events[e]) cudaEventDestroy(ctx->sc.events[e]);
+    if (ctx->h_st) cudaFreeHost(ctx->h_st);
+    if (ctx->h_shift) cudaFreeHost(ctx->h_shift);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,607 @@
+// ccmc_device.cuh -- device building blocks of the CCMC time step.
+//
+// Conventions (shared with the rest of the library, see include/ccmc.h):
+// spin-orbital p is bit (p & 63) of word (p >> 6); 2q = alpha, 2q+1 = beta;
+// the Hartree-Fock (HF) determinant is the lowest N bits; populations are
+// int64 multiples of 2^-16.  Floating point is FP64 without fused
+// multiply-add (the library is compiled with -fmad=false) and every
+// expression below keeps the operation order documented beside it, so that
+// decisions taken from FP64 values (stochastic rounding) are reproducible.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ccmc {
+
+typedef unsigned long long u64;
+typedef long long i64;
+
+constexpr int MAXK = 3;            // words per determinant (M <= 192)
+constexpr int RANK_STRIDE = 200;   // row stride of the rank tables
+constexpr double FIX_ONE = 65536.0;
+
+// Philox counter tags (bits 56..63 of counter word 1).
+enum : u64 {
+    TAG_SAMPLE = 1,      // cluster selection of sample g
+    TAG_SAMPLE_ATT = 2,  // spawning attempt m of sample g
+    TAG_VISIT = 3,       // full non-composite death draw of list entry i
+    TAG_VISIT_ATT = 4,   // full non-composite attempt m of list entry i
+    TAG_THRESH = 5       // occupation threshold of the excitor with a given key
+};
+
+// Device error bits (sticky status word).
+enum : unsigned {
+    ERRB_SPAWN_OVERFLOW = 1u,
+    ERRB_NUMERIC = 2u,
+    ERRB_LIST_OVERFLOW = 4u,
+    ERRB_CLUSTER_OVERFLOW = 8u
+};
+
+// Hamiltonian and generator tables as seen by the kernels (passed by value).
+struct SysDev {
+    int kind;            // 0 UEG, 1 generic
+    int nel, nso, lmax;
+    int nw;
+    u64 hf[MAXK];
+    u64 valid[MAXK];     // bits < nso
+    u64 virt[MAXK];      // bits in [nel, nso)
+    // UEG
+    int nmax, side;
+    const int *grid;     // (2 nmax + 1)^3 -> spatial orbital or -1
+    const int *kv;       // 3 ints per spatial orbital
+    const double *tkin;  // per spin-orbital
+    const double *vtab;  // Coulomb by integer |n|^2
+    double inv_pgen_ueg;
+    u64 npairs, nvirt;
+    // generic integrals
+    int norb;
+    const double *h1;
+    const double *eri;
+    int nv[2];
+    u64 ns_nd, ns;
+    u64 ndcase[3];
+    double inv_pgen_single[2];
+    double inv_pgen_double[3];
+    // rank key: tab[c * RANK_STRIDE + q] = sum_{j=0}^{l-c} C(q, j)
+    const u64 *rank_tab;
+    u64 cocc;
+    double ehf_rel;      // <HF|H|HF> without the core constant
+};
+
+template <int K>
+struct Det {
+    u64 w[K];
+};
+
+// ---------------------------------------------------------------------------
+// Philox-4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11)
+// ---------------------------------------------------------------------------
+
+struct R4 {
+    u64 v[4];
+};
+
+__device__ __forceinline__ R4 philox(u64 c0, u64 c1, u64 c2, u64 c3, u64 k0, u64 k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        const u64 m0 = 0xD2E7470EE14C6C93ULL, m1 = 0xCA5A826395121157ULL;
+        u64 hi0 = __umul64hi(m0, c0), lo0 = m0 * c0;
+        u64 hi1 = __umul64hi(m1, c2), lo1 = m1 * c2;
+        u64 n0 = hi1 ^ c1 ^ k0;
+        u64 n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B97F4A7C15ULL;
+        k1 += 0xBB67AE8584CAA73BULL;
+    }
+    R4 o;
+    o.v[0] = c0;
+    o.v[1] = c1;
+    o.v[2] = c2;
+    o.v[3] = c3;
+    return o;
+}
+
+__device__ __forceinline__ R4 draw(u64 k0, u64 k1, u64 it, u64 tag, u64 index, u64 block)
+{
+    return philox(it, (tag << 56) | index, block, 0, k0, k1);
+}
+
+// uniform in [0,1) from the top 53 bits
+__device__ __forceinline__ double unif(u64 r) { return (double)(r >> 11) * 0x1p-53; }
+
+// integer in [0, n): high word of r*n
+__device__ __forceinline__ u64 below(u64 r, u64 n) { return __umul64hi(r, n); }
+
+// ---------------------------------------------------------------------------
+// Bit strings
+// ---------------------------------------------------------------------------
+
+template <int K>
+__device__ __forceinline__ int bit(const Det<K> &d, int p) { return (int)((d.w[p >> 6] >> (p & 63)) & 1ULL); }
+
+template <int K>
+__device__ __forceinline__ void flip(Det<K> &d, int p) { d.w[p >> 6] ^= 1ULL << (p & 63); }
+
+// number of set bits strictly below position p
+template <int K>
+__device__ __forceinline__ int count_below(const Det<K> &d, int p)
+{
+    int c = 0, wp = p >> 6;
+#pragma unroll
+    for (int i = 0; i < K; i++) {
+        if (i < wp) c += __popcll(d.w[i]);
+        else if (i == wp) c += __popcll(d.w[i] & ((1ULL << (p & 63)) - 1ULL));
+    }
+    return c;
+}
+
+// position of the k-th (0-based) set bit of x; x must have more than k bits
+__device__ __forceinline__ int kth_bit64(u64 x, int k)
+{
+    int pos = 0, c;
+    c = __popc((unsigned)x);
+    if (k >= c) { k -= c; x >>= 32; pos += 32; }
+    c = __popc((unsigned)(x & 0xFFFFULL));
+    if (k >= c) { k -= c; x >>= 16; pos += 16; }
+    c = __popc((unsigned)(x & 0xFFULL));
+    if (k >= c) { k -= c; x >>= 8; pos += 8; }
+    c = __popc((unsigned)(x & 0xFULL));
+    if (k >= c) { k -= c; x >>= 4; pos += 4; }
+    c = __popc((unsigned)(x & 0x3ULL));
+    if (k >= c) { k -= c; x >>= 2; pos += 2; }
+    if (k >= (int)(x & 1ULL)) pos += 1;
+    return pos;
+}
+
+__device__ __forceinline__ u64 spin_mask(int spin)
+{
+    return spin < 0 ? ~0ULL : (spin == 0 ? 0x5555555555555555ULL : 0xAAAAAAAAAAAAAAAAULL);
+}
+
+// k-th occupied spin-orbital (ascending)
+template <int K>
+__device__ __forceinline__ int kth_occupied(const Det<K> &d, int k)
+{
+#pragma unroll
+    for (int w = 0; w < K; w++) {
+        int c = __popcll(d.w[w]);
+        if (k < c) return 64 * w + kth_bit64(d.w[w], k);
+        k -= c;
+    }
+    return -1;
+}
+
+// k-th empty spin-orbital (ascending), optionally of one spin
+template <int K>
+__device__ __forceinline__ int kth_empty(const SysDev &s, const Det<K> &d, u64 k, int spin)
+{
+    u64 sm = spin_mask(spin);
+#pragma unroll
+    for (int w = 0; w < K; w++) {
+        u64 m = ~d.w[w] & s.valid[w] & sm;
+        u64 c = (u64)__popcll(m);
+        if (k < c) return 64 * w + kth_bit64(m, (int)k);
+        k -= c;
+    }
+    return -1;
+}
+
+// excitation level relative to HF = number of holes
+template <int K>
+__device__ __forceinline__ int level_of(const SysDev &s, const Det<K> &d)
+{
+    int c = 0;
+#pragma unroll
+    for (int w = 0; w < K; w++) c += __popcll(s.hf[w] & ~d.w[w]);
+    return c;
+}
+
+template <int K>
+__device__ __forceinline__ bool is_hf(const SysDev &s, const Det<K> &d)
+{
+    bool e = true;
+#pragma unroll
+    for (int w = 0; w < K; w++) e = e && (d.w[w] == s.hf[w]);
+    return e;
+}
+
+// s_D = <D|c_D|HF>: annihilating the holes h_1 < ... < h_n of HF in ascending
+// order meets h_m - (m-1) occupied orbitals below h_m; creating the particles
+// in descending order meets the N - n remaining electrons each time.  The sign
+// is therefore (-1)^(sum h_m - n(n-1)/2 + n(N-n)).
+template <int K>
+__device__ __forceinline__ int excitor_sign(const SysDev &s, const Det<K> &d)
+{
+    int n = 0, hsum = 0;
+#pragma unroll
+    for (int w = 0; w < K; w++) {
+        u64 m = s.hf[w] & ~d.w[w];
+        while (m) {
+            int b = __ffsll((long long)m) - 1;
+            hsum += 64 * w + b;
+            n++;
+            m &= m - 1;
+        }
+    }
+    int par = hsum - n * (n - 1) / 2 + n * (s.nel - n);
+    return (par & 1) ? -1 : 1;
+}
+
+// Applies excitor c_e (given by its determinant) to cur: annihilators of its
+// holes in ascending order, then creators of its particles in descending
+// order, accumulating the parity of the occupied orbitals passed.  Returns
+// false if the product vanishes.
+template <int K>
+__device__ __forceinline__ bool apply_excitor(const SysDev &s, const Det<K> &e, Det<K> &cur, int &parity)
+{
+#pragma unroll
+    for (int w = 0; w < K; w++) {
+        u64 m = s.hf[w] & ~e.w[w];
+        while (m) {
+            int p = 64 * w + (__ffsll((long long)m) - 1);
+            if (!bit(cur, p)) return false;
+            parity += count_below(cur, p);
+            flip(cur, p);
+            m &= m - 1;
+        }
+    }
+#pragma unroll
+    for (int w = K - 1; w >= 0; w--) {
+        u64 m = e.w[w] & s.virt[w];
+        while (m) {
+            int b = 63 - __clzll((long long)m);
+            int p = 64 * w + b;
+            if (bit(cur, p)) return false;
+            parity += count_below(cur, p);
+            flip(cur, p);
+            m &= ~(1ULL << b);
+        }
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Rank key: key = rank_V * C_O - rank_H (order-preserving on level <= l)
+// ---------------------------------------------------------------------------
+
+template <int K>
+__device__ __forceinline__ u64 rank_key(const SysDev &s, const Det<K> &d)
+{
+    u64 rv = 0, rh = 0;
+    int c = 0;
+#pragma unroll
+    for (int w = K - 1; w >= 0; w--) {
+        u64 m = d.w[w] & s.virt[w];
+        while (m) {
+            int b = 63 - __clzll((long long)m);
+            rv += __ldg(&s.rank_tab[c * RANK_STRIDE + (64 * w + b - s.nel)]);
+            c++;
+            m &= ~(1ULL << b);
+        }
+    }
+    c = 0;
+#pragma unroll
+    for (int w = K - 1; w >= 0; w--) {
+        u64 m = s.hf[w] & ~d.w[w];
+        while (m) {
+            int b = 63 - __clzll((long long)m);
+            rh += __ldg(&s.rank_tab[c * RANK_STRIDE + (64 * w + b)]);
+            c++;
+            m &= ~(1ULL << b);
+        }
+    }
+    return rv * s.cocc - rh;
+}
+
+template <int K>
+__device__ __forceinline__ Det<K> unrank_key(const SysDev &s, u64 key)
+{
+    Det<K> d;
+#pragma unroll
+    for (int w = 0; w < K; w++) d.w[w] = s.hf[w];
+    u64 rv = (key + s.cocc - 1) / s.cocc;
+    u64 rh = rv * s.cocc - key;
+    int c = 0;
+    for (int q = s.nso - s.nel - 1; q >= 0 && c <= s.lmax; q--) {
+        u64 cnt = __ldg(&s.rank_tab[c * RANK_STRIDE + q]);
+        if (rv >= cnt) {
+            rv -= cnt;
+            flip(d, q + s.nel);
+            c++;
+        }
+    }
+    c = 0;
+    for (int q = s.nel - 1; q >= 0 && c <= s.lmax; q--) {
+        u64 cnt = __ldg(&s.rank_tab[c * RANK_STRIDE + q]);
+        if (rh >= cnt) {
+            rh -= cnt;
+            flip(d, q);
+            c++;
+        }
+    }
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// Matrix elements (Slater-Condon rules)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int ueg_n2(const SysDev &s, int p, int q)
+{
+    const int *a = s.kv + 3 * (p >> 1), *b = s.kv + 3 * (q >> 1);
+    int dx = __ldg(a) - __ldg(b), dy = __ldg(a + 1) - __ldg(b + 1), dz = __ldg(a + 2) - __ldg(b + 2);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+__device__ __forceinline__ double eri_at(const SysDev &s, int p, int q, int r, int t)
+{
+    size_t n = (size_t)s.norb;
+    return __ldg(&s.eri[((p * n + q) * n + r) * n + t]);
+}
+
+// physicists' <pq|rs> for a momentum-conserving (UEG) or any (generic) quadruple
+__device__ __forceinline__ double g2(const SysDev &s, int p, int q, int r, int t)
+{
+    if (((p ^ r) & 1) || ((q ^ t) & 1)) return 0.0;
+    if (s.kind == 0) return __ldg(&s.vtab[ueg_n2(s, p, r)]);
+    return eri_at(s, p >> 1, r >> 1, q >> 1, t >> 1);
+}
+
+// <D|H|D> without the core constant: one-body sum over occupied p ascending,
+// then the pair sum over p < q ascending (UEG: Tsum - Xsum; generic: e1 + e2).
+template <int K>
+__device__ double diag_abs(const SysDev &s, const Det<K> &d)
+{
+    int occ[64 * MAXK];
+    int n = 0;
+#pragma unroll
+    for (int w = 0; w < K; w++) {
+        u64 m = d.w[w];
+        while (m) {
+            occ[n++] = 64 * w + (__ffsll((long long)m) - 1);
+            m &= m - 1;
+        }
+    }
+    if (s.kind == 0) {
+        double tsum = 0.0, xsum = 0.0;
+        for (int i = 0; i < n; i++) tsum = tsum + __ldg(&s.tkin[occ[i]]);
+        for (int i = 0; i < n; i++)
+            for (int j = i + 1; j < n; j++)
+                if (((occ[i] ^ occ[j]) & 1) == 0) xsum = xsum + __ldg(&s.vtab[ueg_n2(s, occ[i], occ[j])]);
+        return tsum - xsum;
+    }
+    double e1 = 0.0, e2 = 0.0;
+    for (int i = 0; i < n; i++) {
+        int P = occ[i] >> 1;
+        e1 = e1 + __ldg(&s.h1[P * s.norb + P]);
+    }
+    for (int i = 0; i < n; i++)
+        for (int j = i + 1; j < n; j++) {
+            int P = occ[i] >> 1, Q = occ[j] >> 1;
+            double t = eri_at(s, P, P, Q, Q);
+            if (((occ[i] ^ occ[j]) & 1) == 0) t = t - eri_at(s, P, Q, Q, P);
+            e2 = e2 + t;
+        }
+    return e1 + e2;
+}
+
+template <int K>
+__device__ __forceinline__ double diag_rel(const SysDev &s, const Det<K> &d)
+{
+    return diag_abs(s, d) - s.ehf_rel;
+}
+
+// <bra|H|ket> for determinants differing by one or two spin-orbitals.
+// holes i<j are in ket only, particles a<b in bra only; gamma is the phase of
+// a+_a a+_b a_j a_i |ket> = gamma |bra>.
+template <int K>
+__device__ double h_offdiag(const SysDev &s, const Det<K> &ket, int nh, int i, int j, int a, int b)
+{
+    Det<K> cur = ket;
+    int par = count_below(cur, i);
+    flip(cur, i);
+    if (nh == 2) {
+        par += count_below(cur, j);
+        flip(cur, j);
+        par += count_below(cur, b);
+        flip(cur, b);
+    }
+    par += count_below(cur, a);
+    if (nh == 2) {
+        double v1 = g2(s, a, b, i, j);
+        double v2 = g2(s, a, b, j, i);
+        double d = v1 - v2;
+        return (par & 1) ? -d : d;
+    }
+    if (s.kind == 0 || ((i ^ a) & 1)) return 0.0;
+    int A = a >> 1, I = i >> 1;
+    double acc = __ldg(&s.h1[A * s.norb + I]);
+#pragma unroll
+    for (int w = 0; w < K; w++) {
+        u64 m = ket.w[w];
+        while (m) {
+            int k = 64 * w + (__ffsll((long long)m) - 1);
+            m &= m - 1;
+            if (k == i) continue;
+            int Kk = k >> 1;
+            double t = eri_at(s, A, I, Kk, Kk);
+            if (((a ^ k) & 1) == 0) t = t - eri_at(s, A, Kk, Kk, I);
+            acc = acc + t;
+        }
+    }
+    return (par & 1) ? -acc : acc;
+}
+
+// <bra|H|ket> for bra != ket by at most two spin-orbitals (else 0)
+template <int K>
+__device__ double h_between(const SysDev &s, const Det<K> &bra, const Det<K> &ket)
+{
+    int hol[2], par[2], nh = 0, np = 0;
+#pragma unroll
+    for (int w = 0; w < K; w++) {
+        u64 hm = ket.w[w] & ~bra.w[w];
+        u64 pm = bra.w[w] & ~ket.w[w];
+        while (hm) {
+            if (nh < 2) hol[nh] = 64 * w + (__ffsll((long long)hm) - 1);
+            nh++;
+            hm &= hm - 1;
+        }
+        while (pm) {
+            if (np < 2) par[np] = 64 * w + (__ffsll((long long)pm) - 1);
+            np++;
+            pm &= pm - 1;
+        }
+    }
+    if (nh != np || nh == 0 || nh > 2) return 0.0;
+    return h_offdiag(s, ket, nh, hol[0], nh == 2 ? hol[1] : 0, par[0], nh == 2 ? par[1] : 0);
+}
+
+// <HF|H|D> for D at level 1 or 2
+template <int K>
+__device__ __forceinline__ double h_ref(const SysDev &s, const Det<K> &d)
+{
+    Det<K> hf;
+#pragma unroll
+    for (int w = 0; w < K; w++) hf.w[w] = s.hf[w];
+    return h_between(s, hf, d);
+}
+
+// ---------------------------------------------------------------------------
+// Excitation generators
+// ---------------------------------------------------------------------------
+
+// pair index -> (x < y) with index = y(y-1)/2 + x
+__device__ __forceinline__ void pair_of(u64 idx, int &x, int &y)
+{
+    int yy = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)idx)) * 0.5f);
+    if (yy < 1) yy = 1;
+    while ((u64)yy * (yy - 1) / 2 > idx) yy--;
+    while ((u64)(yy + 1) * yy / 2 <= idx) yy++;
+    y = yy;
+    x = (int)(idx - (u64)yy * (yy - 1) / 2);
+}
+
+// One draw of the excitation generator from dj.  Returns false for a null
+// draw; otherwise di, the holes (i<j) and particles (a<b) relative to dj, the
+// number of holes nh and 1/p_gen.
+template <int K>
+__device__ bool excite(const SysDev &s, const Det<K> &dj, const R4 &r, Det<K> &di, int &nh, int &i, int &j,
+                       int &a, int &b, double &inv_pgen)
+{
+    if (s.kind == 0) {
+        int x, y;
+        pair_of(below(r.v[1], s.npairs), x, y);
+        i = kth_occupied(dj, x);
+        j = kth_occupied(dj, y);
+        int aa = kth_empty(s, dj, below(r.v[2], s.nvirt), -1);
+        if (aa < 0) return false;
+        int sb = (i & 1) + (j & 1) - (aa & 1);
+        if (sb < 0 || sb > 1) return false;
+        const int *ki = s.kv + 3 * (i >> 1), *kj = s.kv + 3 * (j >> 1), *ka = s.kv + 3 * (aa >> 1);
+        int nb0 = __ldg(ki) + __ldg(kj) - __ldg(ka);
+        int nb1 = __ldg(ki + 1) + __ldg(kj + 1) - __ldg(ka + 1);
+        int nb2 = __ldg(ki + 2) + __ldg(kj + 2) - __ldg(ka + 2);
+        int nm = s.nmax;
+        if (nb0 < -nm || nb0 > nm || nb1 < -nm || nb1 > nm || nb2 < -nm || nb2 > nm) return false;
+        int bs = __ldg(&s.grid[((nb0 + nm) * s.side + (nb1 + nm)) * s.side + (nb2 + nm)]);
+        if (bs < 0) return false;
+        int bb = 2 * bs + sb;
+        if (bb == aa || bit(dj, bb)) return false;
+        a = aa < bb ? aa : bb;
+        b = aa < bb ? bb : aa;
+        nh = 2;
+        inv_pgen = s.inv_pgen_ueg;
+    } else if (below(r.v[0], s.ns_nd) < s.ns) {
+        i = kth_occupied(dj, (int)below(r.v[1], (u64)s.nel));
+        int sg = i & 1;
+        if (s.nv[sg] == 0) return false;
+        a = kth_empty(s, dj, below(r.v[2], (u64)s.nv[sg]), sg);
+        if (a < 0) return false;
+        j = b = 0;
+        nh = 1;
+        inv_pgen = s.inv_pgen_single[sg];
+    } else {
+        int x, y;
+        pair_of(below(r.v[1], s.npairs), x, y);
+        i = kth_occupied(dj, x);
+        j = kth_occupied(dj, y);
+        int aa, bb, c;
+        if (((i ^ j) & 1) == 0) {
+            int sg = i & 1;
+            c = sg;
+            if (s.ndcase[c] == 0) return false;
+            int xa, ya;
+            pair_of(below(r.v[2], s.ndcase[c]), xa, ya);
+            aa = kth_empty(s, dj, (u64)xa, sg);
+            bb = kth_empty(s, dj, (u64)ya, sg);
+        } else {
+            c = 2;
+            if (s.ndcase[c] == 0) return false;
+            u64 q = below(r.v[2], s.ndcase[c]);
+            aa = kth_empty(s, dj, q / (u64)s.nv[1], 0);
+            bb = kth_empty(s, dj, q % (u64)s.nv[1], 1);
+        }
+        if (aa < 0 || bb < 0) return false;
+        a = aa < bb ? aa : bb;
+        b = aa < bb ? bb : aa;
+        nh = 2;
+        inv_pgen = s.inv_pgen_double[c];
+    }
+    di = dj;
+    flip(di, i);
+    if (nh == 2) flip(di, j);
+    flip(di, a);
+    if (nh == 2) flip(di, b);
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Stochastic rounding onto the 2^-16 grid (below cutoff: +-cutoff with
+// probability |x|/cutoff).  Returns false on overflow of the fixed-point range.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool stoch_round(double x, double u, double cutoff, i64 &out)
+{
+    double ax = fabs(x);
+    if (!(ax < 0x1p46)) {
+        out = 0;
+        return false;
+    }
+    i64 n;
+    if (ax < cutoff) {
+        n = (u * cutoff < ax) ? (i64)(cutoff * FIX_ONE) : 0;
+    } else {
+        double q = ax * FIX_ONE;
+        double f = floor(q);
+        n = (i64)f + ((u < q - f) ? 1 : 0);
+    }
+    out = x < 0.0 ? -n : n;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Neumaier-compensated accumulation
+// ---------------------------------------------------------------------------
+
+struct KSum {
+    double s, c;
+    __device__ __forceinline__ void add(double x)
+    {
+        double t = s + x;
+        if (fabs(s) >= fabs(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ void merge(const KSum &o)
+    {
+        add(o.s);
+        add(o.c);
+    }
+};
+
+}  // namespace ccmc

@@ -1,0 +1,138 @@
+// ccmc_state.cuh -- device-resident state of a CCMC context, shared by the
+// step kernels (ccmc_step.cu) and the host API (ccmc_api.cu).  Every kernel
+// uses a fixed grid and reads its element counts from device memory, so a
+// whole step is issued without a host round trip.
+#pragma once
+
+#include "ccmc_device.cuh"
+
+namespace ccmc {
+
+constexpr int SCAN_THREADS = 512;
+constexpr int WORK_THREADS = 256;
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 8;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+constexpr int MAX_DIGIT_BITS = 8;
+constexpr int RING = 1 << 14;             // per-step records kept on the device
+constexpr int CL_SHIFT = 38;              // packed (clusters << 38) | attempts
+constexpr u64 CL_MASK = (1ULL << CL_SHIFT) - 1ULL;
+
+// Run parameters read by the kernels.
+struct RunParams {
+    double tau;
+    double spawn_cutoff;
+    double a_thresh;
+    u64 seed, replica;
+    int fnc, multispawn;
+};
+
+// Excip list, structure of arrays with capacity cap.
+struct ListView {
+    u64 *bits;      // bits[w * cap + i]
+    u64 *key;
+    i64 *pop;
+    double *diag;   // H_DD - E_HF
+    i64 cap;
+};
+
+// Per-step record as stored on the device (same layout as ccmc_record).
+struct Record {
+    u64 iter;
+    double shift;
+    i64 n0, ntot, n_sel, n_visit, n_attempts, n_spawned;
+    double e_num;
+    i64 ntot_after, nocc_after, n_keys;
+};
+
+// Mutable per-step scalars living in device memory.
+struct DevStep {
+    u64 iter;
+    double shift;
+    i64 n_occ;          // list size at the start of the step
+    i64 ntot, n0, nex, n_sel, fnc_attempts;
+    double mag[8];      // |A_s| of a cluster of size s
+    i64 n_sp;           // spawned records appended (may exceed capacity on overflow)
+    u64 cl_packed;      // (clusters << CL_SHIFT) | attempts of buffered clusters
+    i64 n_attempts;
+    i64 n_keys;         // distinct keys after the reduction
+    i64 kept_list, kept_new;
+    i64 ntot_after;
+    i64 n_start;        // list size at the start of the latest finished step
+    unsigned err;
+    unsigned pad;
+};
+
+// Spawn buffer pair for the radix sort (ping-pong).
+struct SpawnBuf {
+    u64 *key[2];
+    i64 *pop[2];
+    i64 cap;
+};
+
+// Clusters buffered for expanded multi-spawn attempts.
+struct ClusterBuf {
+    u64 *bits;      // bits[w * cap + c]
+    double *catt;   // coefficient of one attempt
+    u64 *index;     // sample index g (Philox counter)
+    i64 *end;       // inclusive attempt prefix
+    i64 cap;
+};
+
+// Per-step work arrays over the list and the merge.
+struct WorkArrays {
+    i64 *prefix;      // inclusive |pop| prefix over entries >= 1 (entry 0: 0)
+    i64 *att_end;     // inclusive prefix of full non-composite attempts
+    double *catt;     // attempt coefficient of each list entry
+    i64 *death;       // death deltas (fixed point)
+    i64 *acc;         // reduced spawned weight matched to each list entry
+    i64 *part;        // block partials of the scans (4 per block)
+    double *enum_part;  // (sum, compensation) per producing block
+    i64 *newpop;      // list values after the merge (threshold applied)
+    i64 *keep_l;      // keep flags of list entries -> exclusive prefix
+    i64 *keep_s;      // keep flags of reduced spawns -> exclusive prefix
+    i64 *ins;         // insertion position of a new key, -1 when matched
+    unsigned *hist;   // radix histograms, digit-major (2^bits x sort grid)
+    Record *ring;     // per-step records
+};
+
+// Grid shapes chosen once per context.
+struct Shapes {
+    int scan_grid;    // blocks of SCAN_THREADS for list scans
+    int work_grid;    // blocks of WORK_THREADS for sampling and attempts
+    int sort_grid;    // blocks of SORT_THREADS for sort passes
+    int digit_bits;   // radix digit width
+    int key_bits;     // significant key bits
+    int enum_slots;   // scan_grid + 2 * work_grid
+};
+
+// Everything the step launcher needs.
+struct StepCtx {
+    int K;
+    SysDev sys;
+    RunParams prm;
+    ListView list[2];
+    int cur;              // list buffer holding the current list
+    SpawnBuf sp;
+    ClusterBuf cl;
+    WorkArrays wa;
+    DevStep *st;          // device scalars
+    Shapes sh;
+    cudaStream_t stream;
+    int sorted_buf;       // spawn buffer holding the sorted records after a step
+    // opt-in phase timers: events[p] is recorded before phase p, events[NPH] after the last
+    bool profile;
+    cudaEvent_t events[8];
+    i64 launches[8];      // kernels launched per phase (cumulative)
+    i64 total_launches;
+};
+
+constexpr int NPHASES = 7;
+
+// Issues one full time step on ctx.stream.  Returns a CUDA error code.
+cudaError_t launch_step(StepCtx &ctx);
+
+// Copies the rank-key bit count needed for a key bound.
+int bits_for(u64 bound);
+
+}  // namespace ccmc

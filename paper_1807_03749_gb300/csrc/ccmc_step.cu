@@ -1,0 +1,1034 @@
+// ccmc_step.cu -- kernels of one CCMC time step (Spencer et al.,
+// arXiv:1807.03749, Sec. II and Sec. IV.B-C) and the launcher that issues
+// them on one stream.
+//
+//  a1  k_scan_partial / k_scan_top / k_scan_final : |t_i| prefix, N_total,
+//      t_HF, N_ex, n_sel, cluster amplitudes; full non-composite visits
+//      (death and estimator of every list entry, Sec. IV.B)
+//  a2-a5 k_sample  : cluster selection, collapse with sign, death, estimator,
+//      one spawning attempt inline or the cluster queued for multi-spawn
+//  a4/a6 k_attempts: expanded multi-spawn attempts (Sec. IV.C)
+//  a7  k_sort_*    : LSD radix sort of spawned records by rank key
+//  a8  k_seg_*     : sum of each run of equal keys
+//  a9  k_merge_*   : merge into the list, occupation threshold, compaction
+//  a10 k_finalize  : projected-energy numerator, per-step record
+#include "ccmc_state.cuh"
+
+namespace ccmc {
+
+#define FULLMASK 0xFFFFFFFFu
+
+// ---------------------------------------------------------------------------
+// Block and warp helpers
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T t = __shfl_up_sync(FULLMASK, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLMASK, v, o);
+    return v;
+}
+
+// inclusive scan of one value per thread; sm must hold 32 elements
+template <typename T>
+__device__ __forceinline__ T block_incl_scan(T v, T *sm, T &total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T incl = warp_incl_scan(v);
+    if (lane == 31) sm[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        T w = lane < nw ? sm[lane] : T(0);
+        T wi = warp_incl_scan(w);
+        if (lane < nw) sm[lane] = wi;
+    }
+    __syncthreads();
+    T off = wid > 0 ? sm[wid - 1] : T(0);
+    total = sm[nw - 1];
+    __syncthreads();
+    return incl + off;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *sm)
+{
+    T tot;
+    block_incl_scan(v, sm, tot);
+    return tot;
+}
+
+// compensated block reduction in a fixed tree order (deterministic)
+__device__ __forceinline__ KSum block_ksum(KSum k, double *sm)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        KSum t;
+        t.s = __shfl_xor_sync(FULLMASK, k.s, o);
+        t.c = __shfl_xor_sync(FULLMASK, k.c, o);
+        k.merge(t);
+    }
+    if (lane == 0) {
+        sm[2 * wid] = k.s;
+        sm[2 * wid + 1] = k.c;
+    }
+    __syncthreads();
+    KSum r = {0.0, 0.0};
+    if (threadIdx.x == 0)
+        for (int w = 0; w < nw; w++) {
+            KSum t = {sm[2 * w], sm[2 * w + 1]};
+            r.merge(t);
+        }
+    __syncthreads();
+    return r;
+}
+
+// contiguous share [lo, hi) of n elements for this block
+__device__ __forceinline__ void chunk_of(i64 n, i64 &lo, i64 &hi)
+{
+    i64 c = (n + gridDim.x - 1) / gridDim.x;
+    lo = (i64)blockIdx.x * c;
+    if (lo > n) lo = n;
+    hi = lo + c;
+    if (hi > n) hi = n;
+}
+
+// All 32 lanes call; returns this lane's exclusive offset in a global
+// counter after reserving the warp's total with one atomic.
+__device__ __forceinline__ i64 warp_reserve(i64 *counter, i64 count)
+{
+    const int lane = threadIdx.x & 31;
+    i64 incl = warp_incl_scan(count);
+    i64 total = __shfl_sync(FULLMASK, incl, 31);
+    i64 base = 0;
+    if (lane == 31 && total) base = (i64)atomicAdd((unsigned long long *)counter, (unsigned long long)total);
+    base = __shfl_sync(FULLMASK, base, 31);
+    return base + incl - count;
+}
+
+__device__ __forceinline__ u64 warp_reserve_u64(u64 *counter, u64 count)
+{
+    const int lane = threadIdx.x & 31;
+    u64 incl = warp_incl_scan(count);
+    u64 total = __shfl_sync(FULLMASK, incl, 31);
+    u64 base = 0;
+    if (lane == 31 && total) base = atomicAdd((unsigned long long *)counter, (unsigned long long)total);
+    base = __shfl_sync(FULLMASK, base, 31);
+    return base + incl - count;
+}
+
+template <int K>
+__device__ __forceinline__ Det<K> load_det(const u64 *bits, i64 cap, i64 i)
+{
+    Det<K> d;
+#pragma unroll
+    for (int w = 0; w < K; w++) d.w[w] = bits[w * cap + i];
+    return d;
+}
+
+template <int K>
+__device__ __forceinline__ void store_det(u64 *bits, i64 cap, i64 i, const Det<K> &d)
+{
+#pragma unroll
+    for (int w = 0; w < K; w++) bits[w * cap + i] = d.w[w];
+}
+
+template <int K>
+__device__ __forceinline__ Det<K> hf_det(const SysDev &s)
+{
+    Det<K> d;
+#pragma unroll
+    for (int w = 0; w < K; w++) d.w[w] = s.hf[w];
+    return d;
+}
+
+// n_attempts = max(1, floor(|A| / A_thresh)) with multi-spawn, else 1
+__device__ __forceinline__ i64 attempts_of(double amp_abs, const RunParams &p)
+{
+    if (!p.multispawn) return 1;
+    double q = floor(amp_abs / p.a_thresh);
+    return q < 1.0 ? 1 : (i64)q;
+}
+
+// smallest i in [1, n-1] with prefix[i] > x (excitor owning position x)
+__device__ __forceinline__ i64 pick_index(const i64 *prefix, i64 n, u64 x)
+{
+    i64 lo = 1, hi = n - 1;
+    while (lo < hi) {
+        i64 mid = lo + (hi - lo) / 2;
+        if ((u64)__ldg(&prefix[mid]) > x) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+// smallest i in [0, n) with end[i] > t
+__device__ __forceinline__ i64 owner_of(const i64 *end, i64 n, i64 t)
+{
+    i64 lo = 0, hi = n - 1;
+    while (lo < hi) {
+        i64 mid = lo + (hi - lo) / 2;
+        if (__ldg(&end[mid]) > t) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+// first i in [0, n) with keys[i] >= k (n if none)
+__device__ __forceinline__ i64 lower_bound_key(const u64 *keys, i64 n, u64 k)
+{
+    i64 lo = 0, hi = n;
+    while (lo < hi) {
+        i64 mid = lo + (hi - lo) / 2;
+        if (__ldg(&keys[mid]) < k) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// One spawning attempt from dj carrying coefficient c_att (Sec. II):
+// value -dtau H_ij c_att s_D(i) / p_gen, stochastically rounded.
+template <int K>
+__device__ __forceinline__ bool spawn_attempt(const SysDev &s, const RunParams &p, const Det<K> &dj, double c_att,
+                                              const R4 &r, u64 &key, i64 &val, unsigned &err)
+{
+    Det<K> di;
+    int nh, i, j, a, b;
+    double inv_pgen;
+    if (!excite(s, dj, r, di, nh, i, j, a, b, inv_pgen)) return false;
+    if (level_of(s, di) > s.lmax) return false;
+    double h = h_offdiag(s, dj, nh, i, j, a, b);
+    double x = ((p.tau * h) * inv_pgen) * c_att;
+    if (excitor_sign(s, di) > 0) x = -x;
+    i64 v;
+    if (!stoch_round(x, unif(r.v[3]), p.spawn_cutoff, v)) {
+        err |= ERRB_NUMERIC;
+        return false;
+    }
+    if (v == 0) return false;
+    key = rank_key(s, di);
+    val = v;
+    return true;
+}
+
+// occupation threshold: 0 < |v| < 1 becomes +-1 with probability |v|, else 0
+__device__ __forceinline__ i64 threshold(const RunParams &p, u64 it, u64 key, i64 v)
+{
+    i64 av = v < 0 ? -v : v;
+    if (av > 0 && av < (i64)FIX_ONE) {
+        R4 r = draw(p.seed, p.replica, it, TAG_THRESH, key, 0);
+        bool keep = (r.v[0] >> 11) < ((u64)av << 37);
+        return keep ? (v < 0 ? -(i64)FIX_ONE : (i64)FIX_ONE) : 0;
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// a1: scans over the list
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_partial(ListView L, DevStep *st, RunParams p, WorkArrays wa)
+{
+    __shared__ i64 sm[32];
+    i64 n = st->n_occ, lo, hi;
+    chunk_of(n, lo, hi);
+    i64 sw = 0, sa = 0;
+    for (i64 i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        i64 v = L.pop[i], av = v < 0 ? -v : v;
+        if (i > 0) sw += av;
+        if (p.fnc) sa += attempts_of(fabs((double)v / FIX_ONE), p);
+    }
+    sw = block_sum(sw, sm);
+    sa = block_sum(sa, sm);
+    if (threadIdx.x == 0) {
+        wa.part[4 * blockIdx.x] = sw;
+        wa.part[4 * blockIdx.x + 1] = sa;
+    }
+}
+
+// one block of 1024 threads; grid <= 1024 partials
+__global__ void __launch_bounds__(1024) k_scan_top(ListView L, DevStep *st, RunParams p, WorkArrays wa, int grid, int lmax)
+{
+    __shared__ i64 sm[32];
+    int t = threadIdx.x;
+    i64 sw = t < grid ? wa.part[4 * t] : 0;
+    i64 sa = t < grid ? wa.part[4 * t + 1] : 0;
+    i64 tw, ta;
+    i64 iw = block_incl_scan(sw, sm, tw);
+    i64 ia = block_incl_scan(sa, sm, ta);
+    if (t < grid) {
+        wa.part[4 * t + 2] = iw - sw;
+        wa.part[4 * t + 3] = ia - sa;
+    }
+    if (t == 0) {
+        i64 n0 = st->n_occ > 0 ? L.pop[0] : 0;
+        i64 an0 = n0 < 0 ? -n0 : n0;
+        i64 ntot = an0 + tw;
+        i64 n_sel = (ntot + 32768) >> 16;
+        st->n0 = n0;
+        st->ntot = ntot;
+        st->nex = tw;
+        st->n_sel = n_sel;
+        st->fnc_attempts = p.fnc ? ta : 0;
+        // |A_s| = N_ex^s / (|t_HF|^(s-1) n_sel p(s) s!), fixed operation order
+        double nex_d = (double)tw / FIX_ONE;
+        double n0_d = (double)an0 / FIX_ONE;
+        int smax = lmax + 2;
+        for (int s = 0; s < 8; s++) st->mag[s] = 0.0;
+        for (int s = 0; s <= smax && n_sel > 0; s++) {
+            double pr;
+            if (p.fnc) {
+                if (s < 2) continue;
+                pr = s < smax ? ldexp(1.0, -(s - 1)) : ldexp(1.0, -lmax);
+            } else {
+                pr = s < smax ? ldexp(1.0, -(s + 1)) : ldexp(1.0, -(lmax + 2));
+            }
+            if (s == 0) {
+                st->mag[0] = n0_d / ((double)n_sel * pr);
+                continue;
+            }
+            double num = 1.0, den = 1.0, fact = 1.0;
+            for (int e = 0; e < s; e++) num = num * nex_d;
+            for (int e = 0; e < s - 1; e++) den = den * n0_d;
+            for (int e = 2; e <= s; e++) fact = fact * (double)e;
+            den = den * (double)n_sel;
+            den = den * pr;
+            den = den * fact;
+            st->mag[s] = num / den;
+        }
+        st->n_sp = 0;
+        st->cl_packed = 0;
+        st->n_attempts = 0;
+        st->n_keys = 0;
+        st->kept_list = 0;
+        st->kept_new = 0;
+        st->ntot_after = 0;
+    }
+}
+
+// prefix arrays; with full non-composite sampling also every visit's death,
+// estimator contribution and attempt coefficient (Sec. IV.B)
+template <int K>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(SysDev s, ListView L, DevStep *st, RunParams p, WorkArrays wa)
+{
+    __shared__ i64 sm[32];
+    __shared__ double smd[64];
+    i64 n = st->n_occ, lo, hi;
+    chunk_of(n, lo, hi);
+    i64 cw = wa.part[4 * blockIdx.x + 2], ca = wa.part[4 * blockIdx.x + 3];
+    const u64 it = st->iter;
+    const double S = st->shift;
+    KSum es = {0.0, 0.0};
+    unsigned err = 0;
+    for (i64 base = lo; base < hi; base += blockDim.x) {
+        i64 i = base + threadIdx.x;
+        bool ok = i < hi;
+        i64 v = ok ? L.pop[i] : 0, av = v < 0 ? -v : v;
+        i64 w = (ok && i > 0) ? av : 0;
+        double amp = (double)v / FIX_ONE;
+        i64 na = (ok && p.fnc) ? attempts_of(fabs(amp), p) : 0;
+        i64 tw, ta;
+        i64 iw = block_incl_scan(w, sm, tw);
+        i64 ia = block_incl_scan(na, sm, ta);
+        if (ok) {
+            wa.prefix[i] = cw + iw;
+            wa.acc[i] = 0;
+            i64 dv = 0;
+            if (p.fnc) {
+                wa.att_end[i] = ca + ia;
+                Det<K> d = load_det<K>(L.bits, L.cap, i);
+                int sd = excitor_sign(s, d);
+                double coef = sd > 0 ? amp : -amp;
+                int lev = level_of(s, d);
+                if (lev == 1 || lev == 2) es.add(h_ref(s, d) * coef);
+                R4 r = draw(p.seed, p.replica, it, TAG_VISIT, (u64)i, 0);
+                double dE = i == 0 ? 0.0 : L.diag[i];
+                double x = (p.tau * (dE - S)) * coef;
+                if (sd > 0) x = -x;
+                if (!stoch_round(x, unif(r.v[0]), 0.0, dv)) err |= ERRB_NUMERIC;
+                wa.catt[i] = na > 1 ? coef / (double)na : coef;
+            }
+            wa.death[i] = dv;
+        }
+        cw += tw;
+        ca += ta;
+    }
+    es = block_ksum(es, smd);
+    if (threadIdx.x == 0) {
+        wa.enum_part[2 * blockIdx.x] = es.s;
+        wa.enum_part[2 * blockIdx.x + 1] = es.c;
+        if (err) atomicOr(&st->err, err);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a2-a5: cluster sampling (Sec. II; composites only with FNC, Sec. IV.B)
+// ---------------------------------------------------------------------------
+
+template <int K>
+__global__ void __launch_bounds__(WORK_THREADS) k_sample(SysDev s, ListView L, DevStep *st, RunParams p, WorkArrays wa,
+                                                         SpawnBuf sp, ClusterBuf cl, int enum_base)
+{
+    __shared__ double smag[8];
+    __shared__ double smd[64];
+    __shared__ i64 sm[32];
+    if (threadIdx.x < 8) smag[threadIdx.x] = st->mag[threadIdx.x];
+    __syncthreads();
+    const i64 n_sel = st->n_sel, n = st->n_occ, nex = st->nex, n0 = st->n0;
+    const u64 it = st->iter;
+    const double S = st->shift;
+    const int lane = threadIdx.x & 31;
+    const i64 nwarps = (i64)gridDim.x * blockDim.x / 32;
+    const i64 wglob = ((i64)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    KSum es = {0.0, 0.0};
+    unsigned err = 0;
+    i64 inline_att = 0;
+    for (i64 g0 = wglob * 32; g0 < n_sel; g0 += nwarps * 32) {
+        const i64 g = g0 + lane;
+        int nrec = 0;
+        u64 rk[2] = {0, 0};
+        i64 rv[2] = {0, 0};
+        bool push = false;
+        Det<K> dj;
+        double catt = 0.0;
+        i64 natt = 0;
+        if (g < n_sel) {
+            R4 r0 = draw(p.seed, p.replica, it, TAG_SAMPLE, (u64)g, 0);
+            u64 nr = ~r0.v[0];
+            int lz = nr ? __clzll((long long)nr) : 64;
+            int sz = p.fnc ? 2 + min(lz, s.lmax) : min(lz, s.lmax + 2);
+            bool valid = true;
+            int par = 0;
+            i64 idx0 = 0;
+            double amp = 0.0;
+            dj = hf_det<K>(s);
+            if (sz == 0) {
+                amp = n0 < 0 ? -smag[0] : smag[0];
+            } else if (nex == 0 || (sz >= 2 && n0 == 0)) {
+                valid = false;
+            } else {
+                R4 r1;
+                if (sz > 2) r1 = draw(p.seed, p.replica, it, TAG_SAMPLE, (u64)g, 1);
+                i64 idx[6];
+                int neg = 0;
+                for (int e = 0; e < sz && valid; e++) {
+                    u64 rr = e < 2 ? r0.v[2 + e] : r1.v[e - 2];
+                    i64 id = pick_index(wa.prefix, n, below(rr, (u64)nex));
+                    for (int f = 0; f < e; f++)
+                        if (idx[f] == id) valid = false;   // repeated excitor: discarded
+                    idx[e] = id;
+                    if (!valid) break;
+                    if (L.pop[id] < 0) neg ^= 1;
+                    Det<K> de = load_det<K>(L.bits, L.cap, id);
+                    if (!apply_excitor(s, de, dj, par)) valid = false;   // shared orbital
+                }
+                if (valid) {
+                    if (n0 < 0 && ((sz - 1) & 1)) neg ^= 1;
+                    amp = neg ? -smag[sz] : smag[sz];
+                    idx0 = idx[0];
+                }
+            }
+            int lev = valid ? level_of(s, dj) : 0;
+            if (valid && lev <= s.lmax + 2) {
+                double coef = (par & 1) ? -amp : amp;
+                if (lev == 1 || lev == 2) es.add(h_ref(s, dj) * coef);
+                int sdj = excitor_sign(s, dj);
+                if (sz <= 1) {
+                    double dE = sz == 0 ? 0.0 : L.diag[idx0];
+                    double x = (p.tau * (dE - S)) * coef;
+                    if (sdj > 0) x = -x;
+                    i64 dv;
+                    if (!stoch_round(x, unif(r0.v[1]), 0.0, dv)) err |= ERRB_NUMERIC;
+                    if (dv != 0) atomicAdd((unsigned long long *)&wa.death[idx0], (unsigned long long)dv);
+                } else if (lev <= s.lmax) {
+                    double x = (p.tau * (diag_rel(s, dj) - S)) * coef;
+                    if (sdj > 0) x = -x;
+                    i64 dv;
+                    if (!stoch_round(x, unif(r0.v[1]), 0.0, dv)) err |= ERRB_NUMERIC;
+                    if (dv != 0) {
+                        rk[nrec] = rank_key(s, dj);
+                        rv[nrec] = dv;
+                        nrec++;
+                    }
+                }
+                natt = attempts_of(fabs(amp), p);
+                if (p.multispawn) {
+                    push = true;
+                    catt = natt > 1 ? coef / (double)natt : coef;
+                } else {
+                    inline_att++;
+                    R4 ra = draw(p.seed, p.replica, it, TAG_SAMPLE_ATT, (u64)g, 0);
+                    u64 k;
+                    i64 v;
+                    if (spawn_attempt(s, p, dj, coef, ra, k, v, err)) {
+                        rk[nrec] = k;
+                        rv[nrec] = v;
+                        nrec++;
+                    }
+                }
+            }
+        }
+        // convergent appends
+        i64 off = warp_reserve(&st->n_sp, nrec);
+        for (int q = 0; q < nrec; q++) {
+            if (off + q < sp.cap) {
+                sp.key[0][off + q] = rk[q];
+                sp.pop[0][off + q] = rv[q];
+            } else {
+                err |= ERRB_SPAWN_OVERFLOW;
+            }
+        }
+        if (p.multispawn) {
+            u64 mine = push ? ((1ULL << CL_SHIFT) | (u64)natt) : 0ULL;
+            u64 o = warp_reserve_u64(&st->cl_packed, mine);
+            if (push) {
+                i64 c = (i64)(o >> CL_SHIFT);
+                i64 a0 = (i64)(o & CL_MASK);
+                if (c < cl.cap) {
+                    store_det<K>(cl.bits, cl.cap, c, dj);
+                    cl.catt[c] = catt;
+                    cl.index[c] = (u64)g;
+                    cl.end[c] = a0 + natt;
+                } else {
+                    err |= ERRB_CLUSTER_OVERFLOW;
+                }
+            }
+        }
+    }
+    es = block_ksum(es, smd);
+    inline_att = block_sum(inline_att, sm);
+    if (threadIdx.x == 0) {
+        wa.enum_part[2 * (enum_base + blockIdx.x)] = es.s;
+        wa.enum_part[2 * (enum_base + blockIdx.x) + 1] = es.c;
+        if (inline_att) atomicAdd((unsigned long long *)&st->n_attempts, (unsigned long long)inline_att);
+        if (err) atomicOr(&st->err, err);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a4/a6: expanded spawning attempts -- full non-composite visits first, then
+// buffered composite clusters (Sec. IV.B-C)
+// ---------------------------------------------------------------------------
+
+template <int K>
+__global__ void __launch_bounds__(WORK_THREADS) k_attempts(SysDev s, ListView L, DevStep *st, RunParams p, WorkArrays wa,
+                                                           SpawnBuf sp, ClusterBuf cl)
+{
+    const i64 n = st->n_occ, tf = st->fnc_attempts;
+    i64 ncl = (i64)(st->cl_packed >> CL_SHIFT);
+    if (ncl > cl.cap) ncl = cl.cap;
+    const i64 tc = ncl > 0 ? cl.end[ncl - 1] : 0;
+    const i64 total = tf + tc;
+    const u64 it = st->iter;
+    const int lane = threadIdx.x & 31;
+    const i64 nwarps = (i64)gridDim.x * blockDim.x / 32;
+    const i64 wglob = ((i64)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    unsigned err = 0;
+    for (i64 t0 = wglob * 32; t0 < total; t0 += nwarps * 32) {
+        const i64 t = t0 + lane;
+        int nrec = 0;
+        u64 k = 0;
+        i64 v = 0;
+        if (t < total) {
+            Det<K> dj;
+            double ca;
+            u64 tag, idx, m;
+            if (t < tf) {
+                i64 i = owner_of(wa.att_end, n, t);
+                m = (u64)(t - (i > 0 ? wa.att_end[i - 1] : 0));
+                dj = load_det<K>(L.bits, L.cap, i);
+                ca = wa.catt[i];
+                tag = TAG_VISIT_ATT;
+                idx = (u64)i;
+            } else {
+                i64 t2 = t - tf;
+                i64 c = owner_of(cl.end, ncl, t2);
+                m = (u64)(t2 - (c > 0 ? cl.end[c - 1] : 0));
+                dj = load_det<K>(cl.bits, cl.cap, c);
+                ca = cl.catt[c];
+                tag = TAG_SAMPLE_ATT;
+                idx = cl.index[c];
+            }
+            R4 r = draw(p.seed, p.replica, it, tag, idx, m);
+            if (spawn_attempt(s, p, dj, ca, r, k, v, err)) nrec = 1;
+        }
+        i64 off = warp_reserve(&st->n_sp, nrec);
+        if (nrec) {
+            if (off < sp.cap) {
+                sp.key[0][off] = k;
+                sp.pop[0][off] = v;
+            } else {
+                err |= ERRB_SPAWN_OVERFLOW;
+            }
+        }
+    }
+    if (err) atomicOr(&st->err, err);
+}
+
+// ---------------------------------------------------------------------------
+// a7: LSD radix sort by rank key (stable, fixed grid, digit-major offsets)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_hist(const u64 *keys, const DevStep *st, i64 cap, int shift, int bits,
+                                                             unsigned *hist)
+{
+    __shared__ unsigned h[1 << MAX_DIGIT_BITS];
+    const int nd = 1 << bits;
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) h[d] = 0;
+    __syncthreads();
+    i64 n = st->n_sp < cap ? st->n_sp : cap, lo, hi;
+    chunk_of(n, lo, hi);
+    const u64 mask = (u64)nd - 1;
+    for (i64 i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) hist[(size_t)d * gridDim.x + blockIdx.x] = h[d];
+}
+
+// exclusive scan of the digit-major histogram in place (one block)
+__global__ void __launch_bounds__(1024) k_sort_scan(unsigned *hist, int total)
+{
+    __shared__ i64 sm[32];
+    const int per = (total + blockDim.x - 1) / blockDim.x;
+    const int lo = threadIdx.x * per;
+    const int hi = min(total, lo + per);
+    i64 sum = 0;
+    for (int i = lo; i < hi; i++) sum += hist[i];
+    i64 tot;
+    i64 incl = block_incl_scan(sum, sm, tot);
+    i64 run = incl - sum;
+    for (int i = lo; i < hi; i++) {
+        unsigned v = hist[i];
+        hist[i] = (unsigned)run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const u64 *kin, const i64 *vin, u64 *kout, i64 *vout,
+                                                                const DevStep *st, i64 cap, int shift, int bits,
+                                                                const unsigned *hist)
+{
+    constexpr int NW = SORT_THREADS / 32;
+    __shared__ unsigned s_off[1 << MAX_DIGIT_BITS];
+    __shared__ unsigned s_tot[1 << MAX_DIGIT_BITS];
+    __shared__ unsigned s_w[NW][1 << MAX_DIGIT_BITS];
+    const int nd = 1 << bits;
+    const u64 mask = (u64)nd - 1;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) s_off[d] = hist[(size_t)d * gridDim.x + blockIdx.x];
+    i64 n = st->n_sp < cap ? st->n_sp : cap, lo, hi;
+    chunk_of(n, lo, hi);
+    for (i64 tb = lo; tb < hi; tb += SORT_TILE) {
+        for (int q = threadIdx.x; q < NW * nd; q += blockDim.x) s_w[q / nd][q % nd] = 0;
+        __syncthreads();
+        u64 kk[SORT_ITEMS];
+        i64 vv[SORT_ITEMS];
+        unsigned dg[SORT_ITEMS], rk[SORT_ITEMS];
+        bool ok[SORT_ITEMS];
+#pragma unroll
+        for (int j = 0; j < SORT_ITEMS; j++) {
+            i64 idx = tb + (i64)wid * (32 * SORT_ITEMS) + j * 32 + lane;
+            ok[j] = idx < hi;
+            kk[j] = ok[j] ? kin[idx] : 0;
+            vv[j] = ok[j] ? vin[idx] : 0;
+            unsigned d = (unsigned)((kk[j] >> shift) & mask);
+            dg[j] = d;
+            unsigned peers = __ballot_sync(FULLMASK, ok[j]);
+            for (int b = 0; b < bits; b++) {
+                unsigned bb = __ballot_sync(FULLMASK, (d >> b) & 1u);
+                peers &= ((d >> b) & 1u) ? bb : ~bb;
+            }
+            unsigned base = 0;
+            if (ok[j]) base = s_w[wid][d];
+            __syncwarp();
+            if (ok[j] && (peers & lt) == 0) s_w[wid][d] = base + __popc(peers);
+            __syncwarp();
+            rk[j] = base + __popc(peers & lt);
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+            unsigned run = 0;
+            for (int w = 0; w < NW; w++) {
+                unsigned t = s_w[w][d];
+                s_w[w][d] = run;
+                run += t;
+            }
+            s_tot[d] = run;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < SORT_ITEMS; j++) {
+            if (ok[j]) {
+                unsigned pos = s_off[dg[j]] + s_w[wid][dg[j]] + rk[j];
+                kout[pos] = kk[j];
+                vout[pos] = vv[j];
+            }
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < nd; d += blockDim.x) s_off[d] += s_tot[d];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a8: one record per distinct key with the summed weight
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_seg_count(const u64 *keys, const DevStep *st, i64 cap, i64 *outpop,
+                                                             WorkArrays wa)
+{
+    __shared__ i64 sm[32];
+    i64 n = st->n_sp < cap ? st->n_sp : cap, lo, hi;
+    chunk_of(n, lo, hi);
+    i64 c = 0;
+    for (i64 i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        c += (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+        outpop[i] = 0;
+    }
+    c = block_sum(c, sm);
+    if (threadIdx.x == 0) wa.part[4 * blockIdx.x] = c;
+}
+
+// generic: exclusive scan of part[4b + src] into part[4b + dst], total to *out
+__global__ void __launch_bounds__(1024) k_part_scan(WorkArrays wa, int grid, int src, int dst, i64 *out)
+{
+    __shared__ i64 sm[32];
+    int t = threadIdx.x;
+    i64 v = t < grid ? wa.part[4 * t + src] : 0, tot;
+    i64 incl = block_incl_scan(v, sm, tot);
+    if (t < grid) wa.part[4 * t + dst] = incl - v;
+    if (t == 0) *out = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_seg_write(const u64 *keys, const i64 *pops, const DevStep *st, i64 cap,
+                                                             u64 *outkey, i64 *outpop, WorkArrays wa)
+{
+    __shared__ i64 sm[32];
+    i64 n = st->n_sp < cap ? st->n_sp : cap, lo, hi;
+    chunk_of(n, lo, hi);
+    i64 carry = wa.part[4 * blockIdx.x + 2];
+    const int lane = threadIdx.x & 31;
+    for (i64 base = lo; base < hi; base += blockDim.x) {
+        i64 i = base + threadIdx.x;
+        bool ok = i < hi;
+        u64 k = ok ? keys[i] : 0;
+        i64 v = ok ? pops[i] : 0;
+        i64 head = (ok && (i == 0 || keys[i - 1] != k)) ? 1 : 0;
+        i64 tot;
+        i64 incl = block_incl_scan(head, sm, tot);
+        i64 seg = ok ? carry + incl - 1 : -1;
+        if (head) outkey[seg] = k;
+        // segmented warp sum; the last lane of each run adds it
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            i64 tv = __shfl_up_sync(FULLMASK, v, o);
+            i64 ts = __shfl_up_sync(FULLMASK, seg, o);
+            if (lane >= o && ts == seg) v += tv;
+        }
+        i64 nxt = __shfl_down_sync(FULLMASK, seg, 1);
+        bool last = lane == 31 || nxt != seg;
+        if (ok && last && v != 0) atomicAdd((unsigned long long *)&outpop[seg], (unsigned long long)v);
+        carry += tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a9: merge into the list with the occupation threshold
+// ---------------------------------------------------------------------------
+
+// each reduced key: add to its list entry, or mark it new (thresholded)
+__global__ void __launch_bounds__(WORK_THREADS) k_merge_match(ListView L, DevStep *st, RunParams p, WorkArrays wa,
+                                                               const u64 *rkey, i64 *rpop)
+{
+    const i64 n = st->n_occ, m = st->n_keys;
+    const u64 it = st->iter;
+    for (i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (i64)gridDim.x * blockDim.x) {
+        u64 k = rkey[j];
+        i64 pos = lower_bound_key(L.key, n, k);
+        if (pos < n && L.key[pos] == k) {
+            wa.acc[pos] = rpop[j];
+            wa.ins[j] = -1;
+            wa.keep_s[j] = 0;
+        } else {
+            i64 v = threshold(p, it, k, rpop[j]);
+            rpop[j] = v;
+            wa.ins[j] = pos;
+            wa.keep_s[j] = v != 0 ? 1 : 0;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(WORK_THREADS) k_merge_list(ListView L, DevStep *st, RunParams p, WorkArrays wa)
+{
+    const i64 n = st->n_occ;
+    const u64 it = st->iter;
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+        i64 v = L.pop[i] + wa.death[i] + wa.acc[i];
+        if (i > 0) v = threshold(p, it, L.key[i], v);
+        wa.newpop[i] = v;
+        wa.keep_l[i] = (i == 0 || v != 0) ? 1 : 0;
+    }
+}
+
+// counts of kept list entries (blocks [0, G)) and kept new keys ([G, 2G))
+__global__ void __launch_bounds__(SCAN_THREADS) k_keep_count(const DevStep *st, WorkArrays wa, int G)
+{
+    __shared__ i64 sm[32];
+    const bool second = blockIdx.x >= G;
+    const i64 n = second ? st->n_keys : st->n_occ;
+    const i64 *f = second ? wa.keep_s : wa.keep_l;
+    i64 c = (n + G - 1) / G;
+    i64 b = second ? blockIdx.x - G : blockIdx.x;
+    i64 lo = b * c < n ? b * c : n, hi = lo + c < n ? lo + c : n;
+    i64 s = 0;
+    for (i64 i = lo + threadIdx.x; i < hi; i += blockDim.x) s += f[i];
+    s = block_sum(s, sm);
+    if (threadIdx.x == 0) wa.part[4 * blockIdx.x] = s;
+}
+
+// exclusive prefixes of the keep flags in place
+__global__ void __launch_bounds__(SCAN_THREADS) k_keep_final(const DevStep *st, WorkArrays wa, int G)
+{
+    __shared__ i64 sm[32];
+    const bool second = blockIdx.x >= G;
+    const i64 n = second ? st->n_keys : st->n_occ;
+    i64 *f = second ? wa.keep_s : wa.keep_l;
+    i64 c = (n + G - 1) / G;
+    i64 b = second ? blockIdx.x - G : blockIdx.x;
+    i64 lo = b * c < n ? b * c : n, hi = lo + c < n ? lo + c : n;
+    i64 carry = wa.part[4 * blockIdx.x + 2];
+    for (i64 base = lo; base < hi; base += blockDim.x) {
+        i64 i = base + threadIdx.x;
+        i64 v = i < hi ? f[i] : 0, tot;
+        i64 incl = block_incl_scan(v, sm, tot);
+        if (i < hi) f[i] = carry + incl - v;
+        carry += tot;
+    }
+}
+
+// scan of the 2G partials: list part then spawn part
+__global__ void __launch_bounds__(1024) k_keep_top(DevStep *st, WorkArrays wa, int G)
+{
+    __shared__ i64 sm[32];
+    int t = threadIdx.x;
+    i64 a = t < G ? wa.part[4 * t] : 0, ta;
+    i64 ia = block_incl_scan(a, sm, ta);
+    if (t < G) wa.part[4 * t + 2] = ia - a;
+    i64 b = t < G ? wa.part[4 * (G + t)] : 0, tb;
+    i64 ib = block_incl_scan(b, sm, tb);
+    if (t < G) wa.part[4 * (G + t) + 2] = ib - b;
+    if (t == 0) {
+        st->kept_list = ta;
+        st->kept_new = tb;
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(WORK_THREADS) k_scatter_list(SysDev s, ListView L, ListView O, DevStep *st, WorkArrays wa,
+                                                                const u64 *rkey)
+{
+    __shared__ i64 sm[32];
+    const i64 n = st->n_occ, m = st->n_keys, kn = st->kept_new;
+    i64 asum = 0;
+    unsigned err = 0;
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+        i64 v = wa.newpop[i];
+        if (!(i == 0 || v != 0)) continue;
+        i64 ub = lower_bound_key(rkey, m, L.key[i]);
+        i64 out = wa.keep_l[i] + (ub < m ? wa.keep_s[ub] : kn);
+        if (out >= O.cap) {
+            err |= ERRB_LIST_OVERFLOW;
+            continue;
+        }
+        store_det<K>(O.bits, O.cap, out, load_det<K>(L.bits, L.cap, i));
+        O.key[out] = L.key[i];
+        O.pop[out] = v;
+        O.diag[out] = L.diag[i];
+        asum += v < 0 ? -v : v;
+    }
+    asum = block_sum(asum, sm);
+    if (threadIdx.x == 0) {
+        if (asum) atomicAdd((unsigned long long *)&st->ntot_after, (unsigned long long)asum);
+        if (err) atomicOr(&st->err, err);
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(WORK_THREADS) k_scatter_new(SysDev s, ListView O, DevStep *st, WorkArrays wa,
+                                                               const u64 *rkey, const i64 *rpop)
+{
+    __shared__ i64 sm[32];
+    const i64 n = st->n_occ, m = st->n_keys, kl = st->kept_list;
+    i64 asum = 0;
+    unsigned err = 0;
+    for (i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (i64)gridDim.x * blockDim.x) {
+        i64 il = wa.ins[j];
+        i64 v = rpop[j];
+        if (il < 0 || v == 0) continue;
+        i64 out = wa.keep_s[j] + (il < n ? wa.keep_l[il] : kl);
+        if (out >= O.cap) {
+            err |= ERRB_LIST_OVERFLOW;
+            continue;
+        }
+        u64 k = rkey[j];
+        Det<K> d = unrank_key<K>(s, k);
+        store_det<K>(O.bits, O.cap, out, d);
+        O.key[out] = k;
+        O.pop[out] = v;
+        O.diag[out] = diag_rel(s, d);
+        asum += v < 0 ? -v : v;
+    }
+    asum = block_sum(asum, sm);
+    if (threadIdx.x == 0) {
+        if (asum) atomicAdd((unsigned long long *)&st->ntot_after, (unsigned long long)asum);
+        if (err) atomicOr(&st->err, err);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a10: estimator reduction and the per-step record
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(1024) k_finalize(DevStep *st, RunParams p, WorkArrays wa, ClusterBuf cl, int slots,
+                                                   i64 list_cap)
+{
+    __shared__ double smd[64];
+    KSum k = {0.0, 0.0};
+    const int per = (slots + blockDim.x - 1) / blockDim.x;
+    for (int q = threadIdx.x * per; q < min(slots, (int)(threadIdx.x + 1) * per); q++) {
+        KSum t = {wa.enum_part[2 * q], wa.enum_part[2 * q + 1]};
+        k.merge(t);
+    }
+    k = block_ksum(k, smd);
+    if (threadIdx.x == 0) {
+        i64 ncl = (i64)(st->cl_packed >> CL_SHIFT);
+        if (ncl > cl.cap) ncl = cl.cap;
+        i64 tc = ncl > 0 ? cl.end[ncl - 1] : 0;
+        Record r;
+        r.iter = st->iter;
+        r.shift = st->shift;
+        r.n0 = st->n0;
+        r.ntot = st->ntot;
+        r.n_sel = st->n_sel;
+        r.n_visit = p.fnc ? st->n_occ : 0;
+        r.n_attempts = st->fnc_attempts + tc + st->n_attempts;
+        r.n_spawned = st->n_sp;
+        r.e_num = k.s + k.c;
+        r.ntot_after = st->ntot_after;
+        r.nocc_after = st->kept_list + st->kept_new;
+        r.n_keys = st->n_keys;
+        wa.ring[st->iter % RING] = r;
+        st->n_start = st->n_occ;
+        st->n_occ = r.nocc_after < list_cap ? r.nocc_after : list_cap;
+        st->iter = st->iter + 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launcher
+// ---------------------------------------------------------------------------
+
+int bits_for(u64 bound)
+{
+    int b = 1;
+    while (b < 64 && (bound - 1) >> b) b++;
+    return b;
+}
+
+template <int K>
+static cudaError_t launch_step_k(StepCtx &c)
+{
+    cudaStream_t sm = c.stream;
+    const Shapes &sh = c.sh;
+    ListView &L = c.list[c.cur];
+    ListView &O = c.list[c.cur ^ 1];
+    WorkArrays &wa = c.wa;
+    auto mark = [&](int phase) {
+        if (c.profile) cudaEventRecord(c.events[phase], sm);
+    };
+
+    // a1
+    mark(0);
+    k_scan_partial<<<sh.scan_grid, SCAN_THREADS, 0, sm>>>(L, c.st, c.prm, wa);
+    k_scan_top<<<1, 1024, 0, sm>>>(L, c.st, c.prm, wa, sh.scan_grid, c.sys.lmax);
+    k_scan_final<K><<<sh.scan_grid, SCAN_THREADS, 0, sm>>>(c.sys, L, c.st, c.prm, wa);
+    c.launches[0] += 3;
+    // a2-a5
+    mark(1);
+    k_sample<K><<<sh.work_grid, WORK_THREADS, 0, sm>>>(c.sys, L, c.st, c.prm, wa, c.sp, c.cl, sh.scan_grid);
+    c.launches[1] += 1;
+    // a4/a6
+    mark(2);
+    if (c.prm.fnc || c.prm.multispawn) {
+        k_attempts<K><<<sh.work_grid, WORK_THREADS, 0, sm>>>(c.sys, L, c.st, c.prm, wa, c.sp, c.cl);
+        c.launches[2] += 1;
+    }
+    // a7: radix sort of the spawned records
+    mark(3);
+    int src = 0;
+    for (int shift = 0; shift < sh.key_bits; shift += sh.digit_bits) {
+        int bits = min(sh.digit_bits, sh.key_bits - shift);
+        k_sort_hist<<<sh.sort_grid, SORT_THREADS, 0, sm>>>(c.sp.key[src], c.st, c.sp.cap, shift, bits, wa.hist);
+        k_sort_scan<<<1, 1024, 0, sm>>>(wa.hist, (1 << bits) * sh.sort_grid);
+        k_sort_scatter<<<sh.sort_grid, SORT_THREADS, 0, sm>>>(c.sp.key[src], c.sp.pop[src], c.sp.key[src ^ 1],
+                                                               c.sp.pop[src ^ 1], c.st, c.sp.cap, shift, bits, wa.hist);
+        src ^= 1;
+        c.launches[3] += 3;
+    }
+    c.sorted_buf = src;
+    const u64 *skey = c.sp.key[src];
+    const i64 *spop = c.sp.pop[src];
+    u64 *rkey = c.sp.key[src ^ 1];
+    i64 *rpop = c.sp.pop[src ^ 1];
+
+    // a8: reduction of equal keys
+    mark(4);
+    k_seg_count<<<sh.scan_grid, SCAN_THREADS, 0, sm>>>(skey, c.st, c.sp.cap, rpop, wa);
+    k_part_scan<<<1, 1024, 0, sm>>>(wa, sh.scan_grid, 0, 2, &c.st->n_keys);
+    k_seg_write<<<sh.scan_grid, SCAN_THREADS, 0, sm>>>(skey, spop, c.st, c.sp.cap, rkey, rpop, wa);
+    c.launches[4] += 3;
+
+    // a9: merge
+    mark(5);
+    k_merge_match<<<sh.work_grid, WORK_THREADS, 0, sm>>>(L, c.st, c.prm, wa, rkey, rpop);
+    k_merge_list<<<sh.work_grid, WORK_THREADS, 0, sm>>>(L, c.st, c.prm, wa);
+    k_keep_count<<<2 * sh.scan_grid, SCAN_THREADS, 0, sm>>>(c.st, wa, sh.scan_grid);
+    k_keep_top<<<1, 1024, 0, sm>>>(c.st, wa, sh.scan_grid);
+    k_keep_final<<<2 * sh.scan_grid, SCAN_THREADS, 0, sm>>>(c.st, wa, sh.scan_grid);
+    k_scatter_list<K><<<sh.work_grid, WORK_THREADS, 0, sm>>>(c.sys, L, O, c.st, wa, rkey);
+    k_scatter_new<K><<<sh.work_grid, WORK_THREADS, 0, sm>>>(c.sys, O, c.st, wa, rkey, rpop);
+    c.launches[5] += 7;
+
+    // a10
+    mark(6);
+    k_finalize<<<1, 1024, 0, sm>>>(c.st, c.prm, wa, c.cl, sh.enum_slots, O.cap);
+    c.launches[6] += 1;
+    mark(7);
+    c.cur ^= 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(StepCtx &c)
+{
+    switch (c.K) {
+    case 1: return launch_step_k<1>(c);
+    case 2: return launch_step_k<2>(c);
+    case 3: return launch_step_k<3>(c);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ccmc

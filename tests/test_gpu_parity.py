@@ -1,0 +1,244 @@
+"""Parity of the CUDA step with the CPU oracle, through the C ABI.
+
+Both sides start from the same oracle-made state and draw the same Philox
+numbers, so lists, populations, spawned records and counters must agree bit
+for bit; the projected-energy numerator (a compensated FP64 sum in a
+different order) must agree to 1e-12 relative.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from ccmc_inputs import molecule_integrals, synthetic_populations, workload
+
+pytestmark = pytest.mark.gpu
+
+INT_FIELDS = ["iter", "n0", "ntot", "n_sel", "n_visit", "n_attempts", "n_spawned", "ntot_after", "nocc_after",
+              "n_keys"]
+
+
+@pytest.fixture(scope="module")
+def ccmc():
+    import paper_1807_03749_gb300 as p
+
+    p.load()
+    return p
+
+
+def _oracle_system(w):
+    if w["kind"] == "ueg":
+        return oracle.System.ueg(w["nel"], w["nso"], w["rs"], w["lmax"])
+    return oracle.System.generic(w["nel"], w["h1"], w["eri"], w["lmax"])
+
+
+def _pair(ccmc, w, **over):
+    w = dict(w)
+    w.update(over)
+    so = _oracle_system(w)
+    keys = ("tau", "target_pop", "d0_init", "shift_a", "zeta", "spawn_cutoff", "fnc", "multispawn", "a_thresh",
+            "seed", "replica")
+    sim = oracle.Sim(so, **{k: w[k] for k in keys if k in w})
+    ctx = ccmc.from_workload(w)
+    return so, sim, ctx
+
+
+def _same_list(sim, ctx):
+    ob, ok, op = sim.get_list()
+    gb, gk, gp = ctx.get_list()
+    assert len(ok) == len(gk)
+    assert np.array_equal(ok, gk)
+    assert np.array_equal(op, gp)
+    assert np.array_equal(ob, gb)
+
+
+def _same_record(orec, grec):
+    o = orec.as_dict() if hasattr(orec, "as_dict") else orec
+    for f in INT_FIELDS:
+        assert o[f] == grec[f], (f, o[f], grec[f])
+    assert o["shift"] == grec["shift"]
+    assert abs(o["e_num"] - grec["e_num"]) <= 1e-12 * max(abs(o["e_num"]), 1e-300)
+
+
+def _same_spawned(sim, ctx):
+    ok_, op_ = sim.spawned()
+    gk, gp = ctx.get_spawned()
+    a = np.lexsort((op_, ok_))
+    b = np.lexsort((gp, gk))
+    assert np.array_equal(ok_[a], gk[b])
+    assert np.array_equal(op_[a], gp[b])
+    assert np.array_equal(sim.death(), ctx.get_death())
+
+
+def _run_lockstep(sim, ctx, nsteps, check_spawned_every=10):
+    for k in range(nsteps):
+        # death deltas belong to the list at the step start: take the oracle's before stepping
+        rec = sim.step()
+        ctx.step(1)
+        grec = ctx.records()[-1]
+        _same_record(rec, grec)
+        if k % check_spawned_every == 0:
+            gk, gp = ctx.get_spawned()
+            ok_, op_ = sim.spawned()
+            a = np.lexsort((op_, ok_))
+            b = np.lexsort((gp, gk))
+            assert np.array_equal(ok_[a], gk[b]) and np.array_equal(op_[a], gp[b])
+        _same_list(sim, ctx)
+
+
+def test_ueg38_ccsd_full_run_bitexact(ccmc):
+    """14 e / 38 spin-orbitals, CCSD, original sampling: the whole 200-step run."""
+    w = workload("ueg14_m38_ccsd")
+    so, sim, ctx = _pair(ccmc, w)
+    _run_lockstep(sim, ctx, w["nsteps"])
+    st = sim.get_state()
+    assert ctx.get_state() == st
+
+
+def test_ueg38_ccsd_shift_phase_bitexact(ccmc):
+    """A low target so that the shift varies: host shift updates match bit for bit."""
+    w = workload("ueg14_m38_ccsd", target_pop=800.0)
+    so, sim, ctx = _pair(ccmc, w)
+    _run_lockstep(sim, ctx, 300, check_spawned_every=50)
+    assert ctx.get_state()[2] is True
+
+
+def test_ueg114_fnc_multispawn_growth_bitexact(ccmc):
+    """14 e / 114 spin-orbitals, CCSDT, full non-composite + multi-spawn: the
+    first 60 steps of the run (two 64-bit words per determinant)."""
+    w = workload("ueg14_m114_ccsdt_fnc_ms")
+    so, sim, ctx = _pair(ccmc, w)
+    _run_lockstep(sim, ctx, 60)
+
+
+def _full_space_state(so, lmax, n_total, seed):
+    keys = so.space_keys(lmax, expand_top=False)
+    dets = [so.unrank(int(k)) for k in keys]
+    levels = [so.level(d) for d in dets]
+    pops = synthetic_populations(levels, n_total, seed)
+    bits = np.stack([so.to_words(d) for d in dets])
+    return bits, pops
+
+
+def test_ueg114_full_size_step_bitexact(ccmc):
+    """The 114 spin-orbital CCSDT workload at full size: every excitor of the
+    108,753-determinant space occupied, N_total = 10^6 (the target), two steps
+    in the library's production launch configuration."""
+    w = workload("ueg14_m114_ccsdt_fnc_ms")
+    so, sim, ctx = _pair(ccmc, w)
+    bits, pops = _full_space_state(so, 3, 1.0e6, seed=21)
+    sim.set_list_words(bits, pops)
+    ctx.set_list(bits, pops)
+    for it in (1500, 1501):
+        sim.set_state(it, -0.35, True, 1.0e6)
+        ctx.set_state(it, -0.35, True, 1.0e6)
+        rec = sim.step()
+        ctx.step(1)
+        _same_record(rec, ctx.records()[-1])
+        assert rec.n_sel > 900_000
+        _same_list(sim, ctx)
+
+
+def test_molecule_all_samplers_bitexact(ccmc):
+    """A small molecule-like Hamiltonian (singles exist, so composite clusters
+    collapse onto the truncated space and composite death is exercised)."""
+    h1, eri = molecule_integrals(norb=8, nocc=3, seed=5, scale=0.3)
+    base = dict(kind="generic", nel=6, norb=8, nso=16, lmax=3, h1=h1, eri=eri, tau=0.01, target_pop=3000.0,
+                d0_init=50.0, shift_a=10, zeta=0.05, spawn_cutoff=2.0 ** -7, a_thresh=1.0, seed=3, replica=0)
+    for fnc, ms in [(0, 0), (1, 0), (0, 1), (1, 1)]:
+        w = dict(base, fnc=fnc, multispawn=ms)
+        so, sim, ctx = _pair(ccmc, w)
+        _run_lockstep(sim, ctx, 80, check_spawned_every=20)
+        ctx.close()
+
+
+def test_three_word_determinants_bitexact(ccmc):
+    """54 e / 162 spin-orbitals (three words per determinant), CCSD."""
+    w = workload("ueg54_m162_ccsd_fp32", precision="fp64", target_pop=1e5, d0_init=200.0)
+    so, sim, ctx = _pair(ccmc, w)
+    _run_lockstep(sim, ctx, 25, check_spawned_every=5)
+
+
+def test_negative_reference_weight(ccmc):
+    """A wavefunction with a negative reference weight evolves identically."""
+    w = workload("ueg14_m38_ccsd")
+    so, sim, ctx = _pair(ccmc, w)
+    sim.run(30)
+    bits, keys, pops = sim.get_list()
+    pops = -pops
+    sim.set_list_words(bits, pops)
+    ctx.set_list(bits, pops)
+    ctx.set_state(*sim.get_state())
+    _run_lockstep(sim, ctx, 20, check_spawned_every=5)
+
+
+def test_death_and_spawned_multisets(ccmc):
+    w = workload("ueg14_m114_ccsdt_fnc_ms")
+    so, sim, ctx = _pair(ccmc, w)
+    for _ in range(15):
+        sim.step()
+        ctx.step(1)
+    _same_spawned(sim, ctx)
+
+
+def test_checkpoint_resume_is_bitexact(ccmc):
+    w = workload("ueg14_m38_ccsd", target_pop=800.0)
+    ctx = ccmc.from_workload(w)
+    ctx.step(40)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        ctx.save(path)
+        ctx.step(30)
+        a = ctx.get_list()
+        sa = ctx.get_state()
+        ctx2 = ccmc.from_workload(w)
+        ctx2.load(path)
+        ctx2.step(30)
+        b = ctx2.get_list()
+        assert ctx2.get_state() == sa
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_spawn_overflow_is_reported(ccmc):
+    """A spawn buffer that is too small yields CCMC_ERR_SPAWN_OVERFLOW, not a fault."""
+    w = workload("ueg14_m38_ccsd", spawn_capacity=64)
+    ctx = ccmc.from_workload(w)
+    with pytest.raises(ccmc.CCMCError) as e:
+        ctx.step(30)
+        ctx.sync()
+    assert e.value.status == 4
+
+
+def test_list_overflow_is_reported(ccmc):
+    w = workload("ueg14_m38_ccsd", list_capacity=16)
+    ctx = ccmc.from_workload(w)
+    with pytest.raises(ccmc.CCMCError) as e:
+        ctx.step(30)
+        ctx.sync()
+    assert e.value.status == 7
+
+
+def test_rejects_bad_lists(ccmc):
+    w = workload("ueg14_m38_ccsd")
+    ctx = ccmc.from_workload(w)
+    hf = np.array([[(1 << 14) - 1]], dtype=np.uint64)
+    with pytest.raises(ccmc.CCMCError):
+        ctx.set_list(np.array([[(1 << 13) - 1]], dtype=np.uint64), np.array([65536]))   # 13 electrons
+    d = ((1 << 14) - 1) ^ 0b11 ^ (0b11 << 14)
+    with pytest.raises(ccmc.CCMCError):
+        ctx.set_list(np.array([[d], [(1 << 14) - 1]], dtype=np.uint64), np.array([65536, 65536]))  # HF not first
+    ctx.set_list(hf, np.array([100 * 65536]))
+
+
+def test_torch_allocator_and_stream(ccmc):
+    """Device memory from PyTorch's caching allocator and a torch stream."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA")
+    w = workload("ueg14_m38_ccsd")
+    s = torch.cuda.Stream()
+    so, sim, ctx = _pair(ccmc, w, use_torch_allocator=True, stream=s.cuda_stream)
+    _run_lockstep(sim, ctx, 30, check_spawned_every=10)
