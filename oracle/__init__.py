@@ -121,6 +121,7 @@ def lib():
             "orc_sim_nspawned": (c_int64, [c_void_p]),
             "orc_sim_get_spawned": (None, [c_void_p, u64p, i64p]),
             "orc_sim_get_death": (None, [c_void_p, i64p]),
+            "orc_sim_ndeath": (c_int64, [c_void_p]),
             "orc_sim_get_record": (None, [c_void_p, POINTER(Record)]),
             "orc_sim_set_state": (None, [c_void_p, c_uint64, c_double, c_int32, c_double]),
             "orc_sim_get_state": (None, [c_void_p, u64p, dp, i32p, dp]),
@@ -390,7 +391,8 @@ class Sim:
         return keys, pop
 
     def death(self) -> np.ndarray:
-        out = np.zeros(self.size(), dtype=np.int64)
+        """Death deltas of the latest step, for the list at that step's start."""
+        out = np.zeros(int(lib().orc_sim_ndeath(self._h)), dtype=np.int64)
         lib().orc_sim_get_death(self._h, out.ctypes.data_as(POINTER(c_int64)))
         return out
 

@@ -677,6 +677,7 @@ typedef struct {
     int64_t *pop;
     /* per-step outputs */
     int64_t *death;
+    int64_t death_n;     /* list size at the start of the latest step */
     int64_t nsp, spcap;
     uint64_t *spkey;
     int64_t *sppop;
@@ -1002,6 +1003,7 @@ static int sim_step_range(orc_sim *m, int propagate_only, int64_t i_lo, int64_t 
     m->enum_sum = 0.0;
     m->enum_comp = 0.0;
     for (int64_t i = 0; i < n; i++) m->death[i] = 0;
+    m->death_n = n;
     /* selection weights |t_i|/(N_total - t_HF), Sec. II */
     int64_t *prefix = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
     if (!prefix) return ORC_ERR_OOM;
@@ -1212,9 +1214,11 @@ void orc_sim_get_spawned(const orc_sim *m, uint64_t *keys, int64_t *pop)
     for (int64_t i = 0; i < m->nsp; i++) { keys[i] = m->spkey[i]; pop[i] = m->sppop[i]; }
 }
 
+int64_t orc_sim_ndeath(const orc_sim *m) { return m->death_n; }
+
 void orc_sim_get_death(const orc_sim *m, int64_t *out)
 {
-    for (int64_t i = 0; i < m->n; i++) out[i] = m->death[i];
+    for (int64_t i = 0; i < m->death_n; i++) out[i] = m->death[i];
 }
 
 void orc_sim_get_record(const orc_sim *m, orc_record *out) { *out = m->rec; }

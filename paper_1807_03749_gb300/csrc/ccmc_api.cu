@@ -642,7 +642,9 @@ ccmc_status ccmc_reference_energy(ccmc_ctx *ctx, double *e_hf)
 ccmc_status ccmc_get_records(ccmc_ctx *ctx, ccmc_record *out, size_t cap, size_t *n)
 {
     if (!ctx || !n) return CCMC_ERR_ARG;
-    CK(cudaStreamSynchronize(ctx->stream));
+    *n = 0;
+    ccmc_status s = check_device(ctx);
+    if (s != CCMC_OK) return s;
     u64 first = ctx->records_read;
     if (ctx->iter > (u64)RING && first < ctx->iter - RING) first = ctx->iter - RING;
     u64 count = ctx->iter - first;

@@ -144,9 +144,9 @@ def test_ueg114_full_size_step_bitexact(ccmc):
 def test_molecule_all_samplers_bitexact(ccmc):
     """A small molecule-like Hamiltonian (singles exist, so composite clusters
     collapse onto the truncated space and composite death is exercised)."""
-    h1, eri = molecule_integrals(norb=8, nocc=3, seed=5, scale=0.3)
+    h1, eri = molecule_integrals(norb=8, nocc=3, seed=5, scale=0.1)
     base = dict(kind="generic", nel=6, norb=8, nso=16, lmax=3, h1=h1, eri=eri, tau=0.01, target_pop=3000.0,
-                d0_init=50.0, shift_a=10, zeta=0.05, spawn_cutoff=2.0 ** -7, a_thresh=1.0, seed=3, replica=0)
+                d0_init=400.0, shift_a=10, zeta=0.05, spawn_cutoff=2.0 ** -7, a_thresh=1.0, seed=3, replica=0)
     for fnc, ms in [(0, 0), (1, 0), (0, 1), (1, 1)]:
         w = dict(base, fnc=fnc, multispawn=ms)
         so, sim, ctx = _pair(ccmc, w)
@@ -204,7 +204,7 @@ def test_checkpoint_resume_is_bitexact(ccmc):
 
 def test_spawn_overflow_is_reported(ccmc):
     """A spawn buffer that is too small yields CCMC_ERR_SPAWN_OVERFLOW, not a fault."""
-    w = workload("ueg14_m38_ccsd", spawn_capacity=64)
+    w = workload("ueg14_m38_ccsd", spawn_capacity=4)
     ctx = ccmc.from_workload(w)
     with pytest.raises(ccmc.CCMCError) as e:
         ctx.step(30)
