@@ -267,8 +267,12 @@ def run_gpu(args, w):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    if args.profile_window:
+        torch.cuda.profiler.start()
     times = timed(args.steps)
     torch.cuda.synchronize()
+    if args.profile_window:
+        torch.cuda.profiler.stop()
     if dist:
         dist.barrier()
     clk = clocks.stop()
@@ -396,6 +400,8 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-window", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args()
     from ccmc_inputs import workload
 

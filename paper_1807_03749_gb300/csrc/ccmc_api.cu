@@ -394,6 +394,23 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     rp.replica = params->replica;
     rp.fnc = params->fnc ? 1 : 0;
     rp.multispawn = params->multispawn ? 1 : 0;
+    rp.a_thresh_one = params->a_thresh == 1.0 ? 1 : 0;
+    {
+        // integer rounding needs a cutoff of 0 or an exact power of two
+        double c = params->spawn_cutoff;
+        int ex = 0;
+        double m = std::frexp(c, &ex);
+        bool pow2 = c == 0.0 || (c > 0.0 && m == 0.5 && ex > -1000 && ex < 1000);
+        rp.int_round = pow2 ? 1 : 0;
+        u64 cb;
+        memcpy(&cb, &c, 8);
+        rp.spawn_rs.cutoff_bits = c > 0.0 ? cb : 0;
+        rp.spawn_rs.cutoff_e = c > 0.0 ? (ex - 1) - 53 : 0;   // u * 2^(ex-1) = mu * 2^(ex-1-53)
+        rp.spawn_rs.cutoff_fixed = (i64)(c * 65536.0);
+        rp.death_rs.cutoff_bits = 0;
+        rp.death_rs.cutoff_e = 0;
+        rp.death_rs.cutoff_fixed = 0;
+    }
 
     // shapes
     int dev = 0, nsm = 148;
@@ -433,6 +450,9 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     WorkArrays &wa = ctx->sc.wa;
     const i64 lc = ctx->list_cap;
     wa.prefix = al.arr<i64>(lc);
+    wa.bucket_bits = 10;
+    while (wa.bucket_bits < 22 && (1LL << wa.bucket_bits) < lc / 2) wa.bucket_bits++;
+    wa.bucket = al.arr<int>(((size_t)1 << wa.bucket_bits) + 1);
     wa.att_end = al.arr<i64>(lc);
     wa.catt = al.arr<double>(lc);
     wa.death = al.arr<i64>(lc);
@@ -444,6 +464,7 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     wa.part = al.arr<i64>(4 * 2 * (size_t)std::max(sh.scan_grid, sh.work_grid));
     wa.enum_part = al.arr<double>(2 * (size_t)sh.enum_slots);
     wa.hist = al.arr<unsigned>((size_t)(1 << MAX_DIGIT_BITS) * sh.sort_grid);
+    wa.hist_tot = al.arr<unsigned>((size_t)(1 << MAX_DIGIT_BITS));
     wa.ring = al.arr<Record>(RING);
     ctx->sc.st = al.arr<DevStep>(1);
     if (al.failed) {

@@ -584,6 +584,79 @@ __device__ __forceinline__ bool stoch_round(double x, double u, double cutoff, i
     return true;
 }
 
+// The same decision taken with integer arithmetic on the FP64 bit pattern.
+// Every FP64 operation of stoch_round is exact -- scaling by 2^16, floor, the
+// subtraction q - f, the 53-bit uniform u and, for a power-of-two cutoff,
+// u * cutoff -- so comparing the exact values as scaled integers reproduces
+// it bit for bit without using the (narrow) FP64 pipe.
+
+// a * 2^sa < b * 2^sb for unsigned a, b
+__host__ __device__ __forceinline__ bool lt_scaled(u64 a, int sa, u64 b, int sb)
+{
+    int d = sa - sb;
+    if (d >= 0) {                       // a * 2^d < b
+        if (a == 0) return b != 0;
+        if (d >= 64) return false;
+        if (d > 0 && (a >> (64 - d)) != 0) return false;
+        return (a << d) < b;
+    }
+    int e = -d;                         // a < b * 2^e
+    if (b == 0) return false;
+    if (e >= 64) return true;
+    if ((b >> (64 - e)) != 0) return true;
+    return a < (b << e);
+}
+
+// |x| = M * 2^E exactly (M < 2^53)
+__host__ __device__ __forceinline__ void split_double(u64 abits, u64 &M, int &E)
+{
+    u64 ex = abits >> 52, fr = abits & ((1ULL << 52) - 1ULL);
+    if (ex == 0) {
+        M = fr;
+        E = -1074;
+    } else {
+        M = fr | (1ULL << 52);
+        E = (int)ex - 1075;
+    }
+}
+
+// Rounding parameters: cutoff must be 0 or a power of two (checked on the host).
+struct RoundSpec {
+    u64 cutoff_bits;   // bit pattern of the cutoff (0 = no cutoff)
+    int cutoff_e;      // u * cutoff = m_u * 2^cutoff_e
+    i64 cutoff_fixed;  // cutoff in fixed point
+};
+
+__host__ __device__ __forceinline__ bool stoch_round_bits(u64 xbits, u64 r, const RoundSpec &rs, i64 &out)
+{
+    const bool neg = (xbits >> 63) != 0;
+    const u64 ab = xbits & 0x7FFFFFFFFFFFFFFFULL;
+    if (!(ab < 0x42D0000000000000ULL)) {   // |x| < 2^46 (also rejects inf and NaN)
+        out = 0;
+        return false;
+    }
+    const u64 mu = r >> 11;                // u = mu * 2^-53
+    u64 M;
+    int E;
+    split_double(ab, M, E);
+    i64 n;
+    if (ab < rs.cutoff_bits) {             // |x| < cutoff
+        n = lt_scaled(mu, rs.cutoff_e, M, E) ? rs.cutoff_fixed : 0;
+    } else {
+        int e = E + 16;                    // q = |x| 2^16 = M 2^e
+        if (e >= 0) {
+            n = (i64)(M << e);
+        } else {
+            int t = -e;
+            u64 f = t >= 64 ? 0 : (M >> t);
+            u64 fr = t >= 64 ? M : (M & ((1ULL << t) - 1ULL));
+            n = (i64)f + (lt_scaled(mu, -53, fr, -t) ? 1 : 0);
+        }
+    }
+    out = neg ? -n : n;
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // Neumaier-compensated accumulation
 // ---------------------------------------------------------------------------

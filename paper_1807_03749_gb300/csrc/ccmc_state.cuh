@@ -25,6 +25,10 @@ struct RunParams {
     double a_thresh;
     u64 seed, replica;
     int fnc, multispawn;
+    int int_round;        // rounding decisions from the FP64 bit pattern (cutoff 0 or 2^k)
+    int a_thresh_one;     // A_thresh == 1: floor(|A|) without a division
+    RoundSpec spawn_rs;   // spawn rounding (with the cutoff)
+    RoundSpec death_rs;   // death rounding (no cutoff)
 };
 
 // Excip list, structure of arrays with capacity cap.
@@ -52,6 +56,9 @@ struct DevStep {
     i64 n_occ;          // list size at the start of the step
     i64 ntot, n0, nex, n_sel, fnc_attempts;
     double mag[8];      // |A_s| of a cluster of size s
+    int bucket_shift;   // selection buckets cover 2^bucket_shift positions each
+    int pad0;
+    i64 nbuckets;
     i64 n_sp;           // spawned records appended (may exceed capacity on overflow)
     u64 cl_packed;      // (clusters << CL_SHIFT) | attempts of buffered clusters
     i64 n_attempts;
@@ -82,6 +89,8 @@ struct ClusterBuf {
 // Per-step work arrays over the list and the merge.
 struct WorkArrays {
     i64 *prefix;      // inclusive |pop| prefix over entries >= 1 (entry 0: 0)
+    int *bucket;      // owner of the first position of each selection bucket
+    int bucket_bits;  // log2 of the bucket capacity
     i64 *att_end;     // inclusive prefix of full non-composite attempts
     double *catt;     // attempt coefficient of each list entry
     i64 *death;       // death deltas (fixed point)
@@ -93,6 +102,7 @@ struct WorkArrays {
     i64 *keep_s;      // keep flags of reduced spawns -> exclusive prefix
     i64 *ins;         // insertion position of a new key, -1 when matched
     unsigned *hist;   // radix histograms, digit-major (2^bits x sort grid)
+    unsigned *hist_tot;  // per-digit totals of the current pass
     Record *ring;     // per-step records
 };
 

@@ -70,10 +70,11 @@ __device__ __forceinline__ T block_sum(T v, T *sm)
     return tot;
 }
 
-// compensated block reduction in a fixed tree order (deterministic)
-__device__ __forceinline__ KSum block_ksum(KSum k, double *sm)
+// compensated block reduction in a fixed tree order (deterministic): a
+// shuffle tree inside each warp, then one more over the warp results, so the
+// chain of dependent FP64 operations is logarithmic in the block size
+__device__ __forceinline__ KSum warp_ksum(KSum k)
 {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         KSum t;
@@ -81,17 +82,26 @@ __device__ __forceinline__ KSum block_ksum(KSum k, double *sm)
         t.c = __shfl_xor_sync(FULLMASK, k.c, o);
         k.merge(t);
     }
+    return k;
+}
+
+__device__ __forceinline__ KSum block_ksum(KSum k, double *sm)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    k = warp_ksum(k);
     if (lane == 0) {
         sm[2 * wid] = k.s;
         sm[2 * wid + 1] = k.c;
     }
     __syncthreads();
     KSum r = {0.0, 0.0};
-    if (threadIdx.x == 0)
-        for (int w = 0; w < nw; w++) {
-            KSum t = {sm[2 * w], sm[2 * w + 1]};
-            r.merge(t);
+    if (wid == 0) {
+        if (lane < nw) {
+            r.s = sm[2 * lane];
+            r.c = sm[2 * lane + 1];
         }
+        r = warp_ksum(r);
+    }
     __syncthreads();
     return r;
 }
@@ -159,14 +169,34 @@ __device__ __forceinline__ Det<K> hf_det(const SysDev &s)
 __device__ __forceinline__ i64 attempts_of(double amp_abs, const RunParams &p)
 {
     if (!p.multispawn) return 1;
+    if (p.a_thresh_one) {
+        // floor(|A|) from the bit pattern (A / 1.0 == A exactly)
+        u64 M;
+        int E;
+        split_double((u64)__double_as_longlong(amp_abs) & 0x7FFFFFFFFFFFFFFFULL, M, E);
+        u64 q = E >= 0 ? (E >= 10 ? (1ULL << 62) : (M << E)) : (E <= -64 ? 0 : (M >> -E));
+        return q < 1 ? 1 : (i64)q;
+    }
     double q = floor(amp_abs / p.a_thresh);
     return q < 1.0 ? 1 : (i64)q;
 }
 
-// smallest i in [1, n-1] with prefix[i] > x (excitor owning position x)
-__device__ __forceinline__ i64 pick_index(const i64 *prefix, i64 n, u64 x)
+// stochastic rounding of a spawned (with cutoff) or death (without) value
+__device__ __forceinline__ bool round_value(double x, u64 r, const RunParams &p, bool spawn, i64 &out)
 {
-    i64 lo = 1, hi = n - 1;
+    if (p.int_round) return stoch_round_bits((u64)__double_as_longlong(x), r, spawn ? p.spawn_rs : p.death_rs, out);
+    return stoch_round(x, unif(r), spawn ? p.spawn_cutoff : 0.0, out);
+}
+
+// smallest i in [1, n-1] with prefix[i] > x (excitor owning position x);
+// the bucket of x brackets the answer between the owners of its first
+// position and of the next bucket's first position
+__device__ __forceinline__ i64 pick_index(const i64 *prefix, const int *bucket, int shift, i64 nbuckets, i64 n,
+                                          u64 x)
+{
+    i64 b = (i64)(x >> shift);
+    i64 lo = __ldg(&bucket[b]);
+    i64 hi = b + 1 < nbuckets ? __ldg(&bucket[b + 1]) : n - 1;
     while (lo < hi) {
         i64 mid = lo + (hi - lo) / 2;
         if ((u64)__ldg(&prefix[mid]) > x) hi = mid;
@@ -175,16 +205,59 @@ __device__ __forceinline__ i64 pick_index(const i64 *prefix, i64 n, u64 x)
     return lo;
 }
 
-// smallest i in [0, n) with end[i] > t
-__device__ __forceinline__ i64 owner_of(const i64 *end, i64 n, i64 t)
+// smallest i in [lo, hi] with end[i] > t (the answer is known to lie there)
+__device__ __forceinline__ i64 owner_in(const i64 *end, i64 lo, i64 hi, i64 t)
 {
-    i64 lo = 0, hi = n - 1;
     while (lo < hi) {
         i64 mid = lo + (hi - lo) / 2;
         if (__ldg(&end[mid]) > t) hi = mid;
         else lo = mid + 1;
     }
     return lo;
+}
+
+// Attempt ranges: entry e owns attempts [end[e-1], end[e]) with end strictly
+// increasing (every entry has at least one attempt), so 32 consecutive
+// entries always cover 32 consecutive attempts.  A warp walks a contiguous
+// chunk of attempts with a sliding window of 32 entry ends (one coalesced
+// load per 32 attempts) and finds each lane's owner by a 5-step search over
+// the window held in registers.
+struct AttemptWindow {
+    i64 cur;      // owner of the first attempt of the current 32
+    i64 prev;     // end[cur - 1] (0 when cur == 0)
+};
+
+__device__ __forceinline__ AttemptWindow window_start(const i64 *end, i64 n, i64 t0)
+{
+    const int lane = threadIdx.x & 31;
+    AttemptWindow w;
+    i64 c = lane == 0 ? owner_in(end, 0, n - 1, t0) : 0;
+    w.cur = __shfl_sync(FULLMASK, c, 0);
+    i64 pv = (lane == 0 && w.cur > 0) ? end[w.cur - 1] : 0;
+    w.prev = __shfl_sync(FULLMASK, pv, 0);
+    return w;
+}
+
+// owner and attempt number of t = t0 + lane; advances the window past t0 + 31
+__device__ __forceinline__ void window_step(const i64 *end, i64 n, i64 t0, AttemptWindow &w, i64 &owner, i64 &m)
+{
+    const int lane = threadIdx.x & 31;
+    const i64 t = t0 + lane;
+    const i64 e = w.cur + lane;
+    const i64 ev = e < n ? __ldg(&end[e]) : 0x7FFFFFFFFFFFFFFFLL;
+    int L = 0;
+#pragma unroll
+    for (int st = 16; st >= 1; st >>= 1) {
+        i64 v = __shfl_sync(FULLMASK, ev, L + st - 1);
+        if (v <= t) L += st;
+    }
+    i64 before = __shfl_sync(FULLMASK, ev, L > 0 ? L - 1 : 0);
+    owner = w.cur + L;
+    m = t - (L > 0 ? before : w.prev);
+    unsigned done = __ballot_sync(FULLMASK, ev <= t0 + 31);
+    int adv = __popc(done);
+    if (adv > 0) w.prev = __shfl_sync(FULLMASK, ev, adv - 1);
+    w.cur += adv;
 }
 
 // first i in [0, n) with keys[i] >= k (n if none)
@@ -214,7 +287,7 @@ __device__ __forceinline__ bool spawn_attempt(const SysDev &s, const RunParams &
     double x = ((p.tau * h) * inv_pgen) * c_att;
     if (excitor_sign(s, di) > 0) x = -x;
     i64 v;
-    if (!stoch_round(x, unif(r.v[3]), p.spawn_cutoff, v)) {
+    if (!round_value(x, r.v[3], p, true, v)) {
         err |= ERRB_NUMERIC;
         return false;
     }
@@ -281,6 +354,11 @@ __global__ void __launch_bounds__(1024) k_scan_top(ListView L, DevStep *st, RunP
         st->n0 = n0;
         st->ntot = ntot;
         st->nex = tw;
+        // selection buckets: the smallest power of two 2^k with N_ex <= 2^(k + bucket_bits)
+        int k = 0;
+        while (k < 62 && ((u64)tw >> (k + wa.bucket_bits)) != 0) k++;
+        st->bucket_shift = k;
+        st->nbuckets = tw > 0 ? (i64)(((u64)tw + (1ULL << k) - 1) >> k) : 0;
         st->n_sel = n_sel;
         st->fnc_attempts = p.fnc ? ta : 0;
         // |A_s| = N_ex^s / (|t_HF|^(s-1) n_sel p(s) s!), fixed operation order
@@ -345,6 +423,13 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(SysDev s, ListView 
         i64 ia = block_incl_scan(na, sm, ta);
         if (ok) {
             wa.prefix[i] = cw + iw;
+            if (i > 0 && w > 0) {
+                // buckets whose first position falls in [prefix[i-1], prefix[i]) start at entry i
+                const int k = st->bucket_shift;
+                u64 p0 = (u64)(cw + iw - w), p1 = (u64)(cw + iw);
+                u64 b0 = (p0 + (1ULL << k) - 1) >> k, b1 = (p1 + (1ULL << k) - 1) >> k;
+                for (u64 b = b0; b < b1; b++) wa.bucket[b] = (int)i;
+            }
             wa.acc[i] = 0;
             i64 dv = 0;
             if (p.fnc) {
@@ -358,7 +443,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(SysDev s, ListView 
                 double dE = i == 0 ? 0.0 : L.diag[i];
                 double x = (p.tau * (dE - S)) * coef;
                 if (sd > 0) x = -x;
-                if (!stoch_round(x, unif(r.v[0]), 0.0, dv)) err |= ERRB_NUMERIC;
+                if (!round_value(x, r.v[0], p, false, dv)) err |= ERRB_NUMERIC;
                 wa.catt[i] = na > 1 ? coef / (double)na : coef;
             }
             wa.death[i] = dv;
@@ -379,7 +464,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(SysDev s, ListView 
 // ---------------------------------------------------------------------------
 
 template <int K>
-__global__ void __launch_bounds__(WORK_THREADS) k_sample(SysDev s, ListView L, DevStep *st, RunParams p, WorkArrays wa,
+__global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(SysDev s, ListView L, DevStep *st, RunParams p, WorkArrays wa,
                                                          SpawnBuf sp, ClusterBuf cl, int enum_base)
 {
     __shared__ double smag[8];
@@ -388,6 +473,8 @@ __global__ void __launch_bounds__(WORK_THREADS) k_sample(SysDev s, ListView L, D
     if (threadIdx.x < 8) smag[threadIdx.x] = st->mag[threadIdx.x];
     __syncthreads();
     const i64 n_sel = st->n_sel, n = st->n_occ, nex = st->nex, n0 = st->n0;
+    const int bshift = st->bucket_shift;
+    const i64 nbk = st->nbuckets;
     const u64 it = st->iter;
     const double S = st->shift;
     const int lane = threadIdx.x & 31;
@@ -424,13 +511,16 @@ __global__ void __launch_bounds__(WORK_THREADS) k_sample(SysDev s, ListView L, D
                 if (sz > 2) r1 = draw(p.seed, p.replica, it, TAG_SAMPLE, (u64)g, 1);
                 i64 idx[6];
                 int neg = 0;
-                for (int e = 0; e < sz && valid; e++) {
+                // the picks are independent: issue all searches before using them
+                for (int e = 0; e < sz; e++) {
                     u64 rr = e < 2 ? r0.v[2 + e] : r1.v[e - 2];
-                    i64 id = pick_index(wa.prefix, n, below(rr, (u64)nex));
+                    idx[e] = pick_index(wa.prefix, wa.bucket, bshift, nbk, n, below(rr, (u64)nex));
+                }
+                for (int e = 1; e < sz; e++)
                     for (int f = 0; f < e; f++)
-                        if (idx[f] == id) valid = false;   // repeated excitor: discarded
-                    idx[e] = id;
-                    if (!valid) break;
+                        if (idx[f] == idx[e]) valid = false;   // repeated excitor: discarded
+                for (int e = 0; e < sz && valid; e++) {
+                    const i64 id = idx[e];
                     if (L.pop[id] < 0) neg ^= 1;
                     Det<K> de = load_det<K>(L.bits, L.cap, id);
                     if (!apply_excitor(s, de, dj, par)) valid = false;   // shared orbital
@@ -451,13 +541,13 @@ __global__ void __launch_bounds__(WORK_THREADS) k_sample(SysDev s, ListView L, D
                     double x = (p.tau * (dE - S)) * coef;
                     if (sdj > 0) x = -x;
                     i64 dv;
-                    if (!stoch_round(x, unif(r0.v[1]), 0.0, dv)) err |= ERRB_NUMERIC;
+                    if (!round_value(x, r0.v[1], p, false, dv)) err |= ERRB_NUMERIC;
                     if (dv != 0) atomicAdd((unsigned long long *)&wa.death[idx0], (unsigned long long)dv);
                 } else if (lev <= s.lmax) {
                     double x = (p.tau * (diag_rel(s, dj) - S)) * coef;
                     if (sdj > 0) x = -x;
                     i64 dv;
-                    if (!stoch_round(x, unif(r0.v[1]), 0.0, dv)) err |= ERRB_NUMERIC;
+                    if (!round_value(x, r0.v[1], p, false, dv)) err |= ERRB_NUMERIC;
                     if (dv != 0) {
                         rk[nrec] = rank_key(s, dj);
                         rv[nrec] = dv;
@@ -524,54 +614,60 @@ __global__ void __launch_bounds__(WORK_THREADS) k_sample(SysDev s, ListView L, D
 // ---------------------------------------------------------------------------
 
 template <int K>
-__global__ void __launch_bounds__(WORK_THREADS) k_attempts(SysDev s, ListView L, DevStep *st, RunParams p, WorkArrays wa,
-                                                           SpawnBuf sp, ClusterBuf cl)
+__global__ void __launch_bounds__(WORK_THREADS, 4) k_attempts(SysDev s, ListView L, DevStep *st, RunParams p,
+                                                              WorkArrays wa, SpawnBuf sp, ClusterBuf cl)
 {
     const i64 n = st->n_occ, tf = st->fnc_attempts;
     i64 ncl = (i64)(st->cl_packed >> CL_SHIFT);
     if (ncl > cl.cap) ncl = cl.cap;
     const i64 tc = ncl > 0 ? cl.end[ncl - 1] : 0;
-    const i64 total = tf + tc;
     const u64 it = st->iter;
     const int lane = threadIdx.x & 31;
     const i64 nwarps = (i64)gridDim.x * blockDim.x / 32;
     const i64 wglob = ((i64)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     unsigned err = 0;
-    for (i64 t0 = wglob * 32; t0 < total; t0 += nwarps * 32) {
-        const i64 t = t0 + lane;
-        int nrec = 0;
-        u64 k = 0;
-        i64 v = 0;
-        if (t < total) {
-            Det<K> dj;
-            double ca;
-            u64 tag, idx, m;
-            if (t < tf) {
-                i64 i = owner_of(wa.att_end, n, t);
-                m = (u64)(t - (i > 0 ? wa.att_end[i - 1] : 0));
-                dj = load_det<K>(L.bits, L.cap, i);
-                ca = wa.catt[i];
-                tag = TAG_VISIT_ATT;
-                idx = (u64)i;
-            } else {
-                i64 t2 = t - tf;
-                i64 c = owner_of(cl.end, ncl, t2);
-                m = (u64)(t2 - (c > 0 ? cl.end[c - 1] : 0));
-                dj = load_det<K>(cl.bits, cl.cap, c);
-                ca = cl.catt[c];
-                tag = TAG_SAMPLE_ATT;
-                idx = cl.index[c];
+    for (int part = 0; part < 2; part++) {
+        // part 0: full non-composite attempts (owners: list entries);
+        // part 1: attempts of the composite clusters queued by k_sample
+        const i64 total = part == 0 ? tf : tc;
+        const i64 *end = part == 0 ? wa.att_end : cl.end;
+        const i64 nown = part == 0 ? n : ncl;
+        const i64 per = ((total + nwarps - 1) / nwarps + 31) & ~31LL;
+        const i64 a0 = wglob * per, a1 = a0 + per < total ? a0 + per : total;
+        if (a0 >= a1) continue;
+        AttemptWindow w = window_start(end, nown, a0);
+        for (i64 t0 = a0; t0 < a1; t0 += 32) {
+            i64 o, m;
+            window_step(end, nown, t0, w, o, m);
+            int nrec = 0;
+            u64 k = 0;
+            i64 v = 0;
+            if (t0 + lane < a1) {
+                Det<K> dj;
+                double ca;
+                u64 tag, idx;
+                if (part == 0) {
+                    dj = load_det<K>(L.bits, L.cap, o);
+                    ca = wa.catt[o];
+                    tag = TAG_VISIT_ATT;
+                    idx = (u64)o;
+                } else {
+                    dj = load_det<K>(cl.bits, cl.cap, o);
+                    ca = cl.catt[o];
+                    tag = TAG_SAMPLE_ATT;
+                    idx = cl.index[o];
+                }
+                R4 r = draw(p.seed, p.replica, it, tag, idx, (u64)m);
+                if (spawn_attempt(s, p, dj, ca, r, k, v, err)) nrec = 1;
             }
-            R4 r = draw(p.seed, p.replica, it, tag, idx, m);
-            if (spawn_attempt(s, p, dj, ca, r, k, v, err)) nrec = 1;
-        }
-        i64 off = warp_reserve(&st->n_sp, nrec);
-        if (nrec) {
-            if (off < sp.cap) {
-                sp.key[0][off] = k;
-                sp.pop[0][off] = v;
-            } else {
-                err |= ERRB_SPAWN_OVERFLOW;
+            i64 off = warp_reserve(&st->n_sp, nrec);
+            if (nrec) {
+                if (off < sp.cap) {
+                    sp.key[0][off] = k;
+                    sp.pop[0][off] = v;
+                } else {
+                    err |= ERRB_SPAWN_OVERFLOW;
+                }
             }
         }
     }
@@ -597,28 +693,27 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_hist(const u64 *keys, con
     for (int d = threadIdx.x; d < nd; d += blockDim.x) hist[(size_t)d * gridDim.x + blockIdx.x] = h[d];
 }
 
-// exclusive scan of the digit-major histogram in place (one block)
-__global__ void __launch_bounds__(1024) k_sort_scan(unsigned *hist, int total)
+// exclusive scan of row d (one digit across all sort blocks) in place, and
+// the row total; one block per digit
+__global__ void __launch_bounds__(1024) k_sort_scan(unsigned *hist, int grid, unsigned *totals)
 {
     __shared__ i64 sm[32];
-    const int per = (total + blockDim.x - 1) / blockDim.x;
-    const int lo = threadIdx.x * per;
-    const int hi = min(total, lo + per);
-    i64 sum = 0;
-    for (int i = lo; i < hi; i++) sum += hist[i];
-    i64 tot;
-    i64 incl = block_incl_scan(sum, sm, tot);
-    i64 run = incl - sum;
-    for (int i = lo; i < hi; i++) {
-        unsigned v = hist[i];
-        hist[i] = (unsigned)run;
-        run += v;
+    const int d = blockIdx.x;
+    unsigned *row = hist + (size_t)d * grid;
+    i64 carry = 0;
+    for (int base = 0; base < grid; base += blockDim.x) {
+        int b = base + threadIdx.x;
+        i64 v = b < grid ? row[b] : 0, tot;
+        i64 incl = block_incl_scan(v, sm, tot);
+        if (b < grid) row[b] = (unsigned)(carry + incl - v);
+        carry += tot;
     }
+    if (threadIdx.x == 0) totals[d] = (unsigned)carry;
 }
 
 __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const u64 *kin, const i64 *vin, u64 *kout, i64 *vout,
                                                                 const DevStep *st, i64 cap, int shift, int bits,
-                                                                const unsigned *hist)
+                                                                const unsigned *hist, const unsigned *totals)
 {
     constexpr int NW = SORT_THREADS / 32;
     __shared__ unsigned s_off[1 << MAX_DIGIT_BITS];
@@ -628,7 +723,18 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const u64 *kin, c
     const u64 mask = (u64)nd - 1;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    for (int d = threadIdx.x; d < nd; d += blockDim.x) s_off[d] = hist[(size_t)d * gridDim.x + blockIdx.x];
+    {
+        // digit base = exclusive scan of the digit totals; plus this block's row prefix
+        __shared__ i64 sm64[32];
+        for (int d0 = 0; d0 < nd; d0 += blockDim.x) {
+            int d = d0 + threadIdx.x;
+            i64 v = d < nd ? totals[d] : 0, tot;
+            i64 incl = block_incl_scan(v, sm64, tot);
+            if (d < nd) s_off[d] = (unsigned)(incl - v);
+            __syncthreads();
+        }
+        for (int d = threadIdx.x; d < nd; d += blockDim.x) s_off[d] += hist[(size_t)d * gridDim.x + blockIdx.x];
+    }
     i64 n = st->n_sp < cap ? st->n_sp : cap, lo, hi;
     chunk_of(n, lo, hi);
     for (i64 tb = lo; tb < hi; tb += SORT_TILE) {
@@ -907,8 +1013,7 @@ __global__ void __launch_bounds__(1024) k_finalize(DevStep *st, RunParams p, Wor
 {
     __shared__ double smd[64];
     KSum k = {0.0, 0.0};
-    const int per = (slots + blockDim.x - 1) / blockDim.x;
-    for (int q = threadIdx.x * per; q < min(slots, (int)(threadIdx.x + 1) * per); q++) {
+    for (int q = threadIdx.x; q < slots; q += blockDim.x) {
         KSum t = {wa.enum_part[2 * q], wa.enum_part[2 * q + 1]};
         k.merge(t);
     }
@@ -982,9 +1087,10 @@ static cudaError_t launch_step_k(StepCtx &c)
     for (int shift = 0; shift < sh.key_bits; shift += sh.digit_bits) {
         int bits = min(sh.digit_bits, sh.key_bits - shift);
         k_sort_hist<<<sh.sort_grid, SORT_THREADS, 0, sm>>>(c.sp.key[src], c.st, c.sp.cap, shift, bits, wa.hist);
-        k_sort_scan<<<1, 1024, 0, sm>>>(wa.hist, (1 << bits) * sh.sort_grid);
+        k_sort_scan<<<1 << bits, 1024, 0, sm>>>(wa.hist, sh.sort_grid, wa.hist_tot);
         k_sort_scatter<<<sh.sort_grid, SORT_THREADS, 0, sm>>>(c.sp.key[src], c.sp.pop[src], c.sp.key[src ^ 1],
-                                                               c.sp.pop[src ^ 1], c.st, c.sp.cap, shift, bits, wa.hist);
+                                                               c.sp.pop[src ^ 1], c.st, c.sp.cap, shift, bits, wa.hist,
+                                                               wa.hist_tot);
         src ^= 1;
         c.launches[3] += 3;
     }

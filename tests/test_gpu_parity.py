@@ -113,6 +113,24 @@ def test_ueg114_fnc_multispawn_growth_bitexact(ccmc):
     _run_lockstep(sim, ctx, 60)
 
 
+def test_ueg114_long_lockstep_and_determinism(ccmc):
+    """600 consecutive steps of the 114 spin-orbital FNC + multi-spawn run in
+    lockstep with the oracle (records every step, lists every 50 steps), and
+    a second context with the same seed reproducing the run exactly."""
+    w = workload("ueg14_m114_ccsdt_fnc_ms")
+    so, sim, ctx = _pair(ccmc, w)
+    twin = ccmc.from_workload(w)
+    for k in range(600):
+        rec = sim.step()
+        ctx.step(1)
+        twin.step(1)
+        g = ctx.records()
+        assert g == twin.records()
+        _same_record(rec, g[-1])
+        if k % 50 == 49:
+            _same_list(sim, ctx)
+
+
 def _full_space_state(so, lmax, n_total, seed):
     keys = so.space_keys(lmax, expand_top=False)
     dets = [so.unrank(int(k)) for k in keys]
