@@ -216,6 +216,32 @@ ccmc_status ccmc_profile(ccmc_ctx *ctx, int32_t enable);
  * number of kernels launched by ccmc_step since the context was created. */
 ccmc_status ccmc_phase_times(ccmc_ctx *ctx, double *ms, int64_t *launches, int32_t nphases, int64_t *total_launches);
 
+/* Largest record count accepted by ccmc_reduce_records_noalloc. */
+#define CCMC_NOALLOC_MAX_RECORDS 65536
+
+/* Sorts n spawned records by key and sums each run of equal keys -- the
+ * annihilation's sort and reduction as a standalone call -- without
+ * allocating anything.  The paper has no counterpart: it is for callers that
+ * cannot call cudaMalloc (code issued inside CUDA graph capture, real-time
+ * loops with a fixed memory budget, hosts that own the device allocator).
+ *   keys_in, pops_in   device arrays of n records (read only)
+ *   key_bits           significant bits of the keys (1..64)
+ *   keys_out, pops_out device arrays with room for n records; receive the
+ *                      distinct keys in increasing order and their summed
+ *                      weights (runs that sum to zero are kept)
+ *   n_out              host pointer; receives the number of distinct keys
+ *   cuda_stream        cudaStream_t for the work (NULL = legacy stream); the
+ *                      call waits for it before returning
+ * Scratch is one fixed 2 MiB device array inside the library, held by every
+ * GPU that loads it until the process exits; n above
+ * CCMC_NOALLOC_MAX_RECORDS is rejected with CCMC_ERR_ARG.  The first call on
+ * a device looks up that array's device address (once per device); make that
+ * first call before any stream capture.  All calls share the array, so calls
+ * that overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller. */
+ccmc_status ccmc_reduce_records_noalloc(const uint64_t *keys_in, const int64_t *pops_in, size_t n, int32_t key_bits,
+                                        uint64_t *keys_out, int64_t *pops_out, size_t *n_out, void *cuda_stream);
+
 /* Waits for the context's stream and reports kernel-detected errors. */
 ccmc_status ccmc_sync(ccmc_ctx *ctx);
 

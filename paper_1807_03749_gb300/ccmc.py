@@ -66,6 +66,7 @@ EXPORTS = [
     "ccmc_init", "ccmc_step", "ccmc_energy", "ccmc_reference_energy", "ccmc_get_records", "ccmc_list_size",
     "ccmc_get_list", "ccmc_set_list", "ccmc_get_spawned", "ccmc_get_death", "ccmc_set_state", "ccmc_get_state",
     "ccmc_save", "ccmc_load", "ccmc_sync", "ccmc_last_error", "ccmc_free", "ccmc_profile", "ccmc_phase_times",
+    "ccmc_reduce_records_noalloc",
 ]
 
 PHASES = ["scan", "sample", "attempts", "sort", "reduce", "merge", "finalize"]
@@ -100,6 +101,7 @@ def load(path: str | None = None):
         "ccmc_free": (None, [vp]),
         "ccmc_profile": (c_int, [vp, c_int32]),
         "ccmc_phase_times": (c_int, [vp, dp, i64p, c_int32, i64p]),
+        "ccmc_reduce_records_noalloc": (c_int, [vp, vp, c_size_t, c_int32, vp, vp, POINTER(c_size_t), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -12,6 +12,9 @@
 //  a8  k_seg_*     : sum of each run of equal keys
 //  a9  k_merge_*   : merge into the list, occupation threshold, compaction
 //  a10 k_finalize  : projected-energy numerator, per-step record
+#include <mutex>
+
+#include "../../include/ccmc.h"
 #include "ccmc_state.cuh"
 
 namespace ccmc {
@@ -1138,3 +1141,109 @@ cudaError_t launch_step(StepCtx &c)
 }
 
 }  // namespace ccmc
+
+// ---------------------------------------------------------------------------
+// Sort-and-reduce of spawned records without any allocation
+//
+// For callers that cannot allocate device memory themselves: code running
+// inside a captured CUDA graph or a pre-sized real-time loop, plugins whose
+// host owns the device allocator, or tools that must not grow the memory
+// footprint.  The scratch lives in one file-scope device array that every
+// GPU loading this library holds until the process exits.
+// ---------------------------------------------------------------------------
+
+namespace ccmc {
+namespace {
+
+constexpr size_t NOALLOC_MAX = (size_t)1 << 16;   // records per call
+constexpr int NOALLOC_GRID = 64;                   // blocks of the sort and reduce kernels
+
+struct NoAllocScratch {
+    u64 key[2][NOALLOC_MAX];
+    i64 pop[2][NOALLOC_MAX];
+    unsigned hist[(1 << MAX_DIGIT_BITS) * NOALLOC_GRID];
+    unsigned tot[1 << MAX_DIGIT_BITS];
+    i64 part[8 * NOALLOC_GRID];
+    DevStep st;
+};
+
+__device__ __align__(256) NoAllocScratch g_noalloc;
+
+std::mutex g_noalloc_mutex;
+NoAllocScratch *g_noalloc_ptr[256];
+
+// Device address of the scratch on the current device, looked up once per
+// device (host code cannot use the symbol itself as a device address).
+cudaError_t noalloc_scratch(NoAllocScratch **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = (NoAllocScratch *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+__global__ void k_noalloc_begin(DevStep *st, i64 n)
+{
+    if (threadIdx.x == 0) {
+        st->n_sp = n;
+        st->n_keys = 0;
+        st->err = 0;
+    }
+}
+
+}  // namespace
+
+}  // namespace ccmc
+
+extern "C" ccmc_status ccmc_reduce_records_noalloc(const uint64_t *keys_in, const int64_t *pops_in, size_t n,
+                                                   int32_t key_bits, uint64_t *keys_out, int64_t *pops_out,
+                                                   size_t *n_out, void *cuda_stream)
+{
+    using namespace ccmc;
+    if (!n_out) return CCMC_ERR_ARG;
+    *n_out = 0;
+    if (n > NOALLOC_MAX || key_bits < 1 || key_bits > 64) return CCMC_ERR_ARG;
+    if (n == 0) return CCMC_OK;
+    if (!keys_in || !pops_in || !keys_out || !pops_out) return CCMC_ERR_ARG;
+    cudaStream_t sm = (cudaStream_t)cuda_stream;
+    NoAllocScratch *S = nullptr;
+    if (noalloc_scratch(&S) != cudaSuccess) return CCMC_ERR_CUDA;
+    const i64 cap = (i64)NOALLOC_MAX;
+    k_noalloc_begin<<<1, 32, 0, sm>>>(&S->st, (i64)n);
+    // LSD radix passes: the caller's input, then the two scratch buffers
+    const u64 *kin = (const u64 *)keys_in;
+    const i64 *vin = (const i64 *)pops_in;
+    int dst = 0;
+    for (int shift = 0; shift < key_bits; shift += MAX_DIGIT_BITS) {
+        int bits = key_bits - shift < MAX_DIGIT_BITS ? key_bits - shift : MAX_DIGIT_BITS;
+        k_sort_hist<<<NOALLOC_GRID, SORT_THREADS, 0, sm>>>(kin, &S->st, cap, shift, bits, S->hist);
+        k_sort_scan<<<1 << bits, 1024, 0, sm>>>(S->hist, NOALLOC_GRID, S->tot);
+        k_sort_scatter<<<NOALLOC_GRID, SORT_THREADS, 0, sm>>>(kin, vin, S->key[dst], S->pop[dst], &S->st, cap, shift,
+                                                               bits, S->hist, S->tot);
+        kin = S->key[dst];
+        vin = S->pop[dst];
+        dst ^= 1;
+    }
+    // one record per distinct key with the summed weight
+    WorkArrays wa;
+    memset(&wa, 0, sizeof(wa));
+    wa.part = S->part;
+    k_seg_count<<<NOALLOC_GRID, SCAN_THREADS, 0, sm>>>(kin, &S->st, cap, (i64 *)pops_out, wa);
+    k_part_scan<<<1, 1024, 0, sm>>>(wa, NOALLOC_GRID, 0, 2, &S->st.n_keys);
+    k_seg_write<<<NOALLOC_GRID, SCAN_THREADS, 0, sm>>>(kin, vin, &S->st, cap, (u64 *)keys_out, (i64 *)pops_out, wa);
+    if (cudaGetLastError() != cudaSuccess) return CCMC_ERR_CUDA;
+    i64 m = 0;
+    if (cudaMemcpyAsync(&m, &S->st.n_keys, sizeof(i64), cudaMemcpyDeviceToHost, sm) != cudaSuccess) return CCMC_ERR_CUDA;
+    if (cudaStreamSynchronize(sm) != cudaSuccess) return CCMC_ERR_CUDA;
+    *n_out = (size_t)m;
+    return CCMC_OK;
+}
