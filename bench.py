@@ -306,13 +306,7 @@ def run_gpu(args, w):
     alg = algorithmic_bytes(dom, precs, ctx.nw)
     hbm, src = peaks()
     achieved = alg / (dom_ms * 1e-3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", f"traffic_{w['name']}.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get(dom)
-        except Exception:
-            traffic = None
+    traffic = read_traffic(w["name"], dom)
 
     # end-to-end through the public API with host buffers: upload the excip
     # list, one step, download the list and the estimators
@@ -367,6 +361,20 @@ def run_gpu(args, w):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def read_traffic(workload: str, phase: str):
+    """DRAM bytes per launch of a phase's kernel from the committed ncu summary
+    (profiles/traffic_<workload>.txt), or None."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.txt")
+    try:
+        for line in open(path):
+            f = line.split()
+            if len(f) == 3 and not line.startswith("#") and f[0] == phase:
+                return float(f[2])
+    except OSError:
+        pass
+    return None
 
 
 def cpu_baseline(w):

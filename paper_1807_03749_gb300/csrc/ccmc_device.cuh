@@ -10,6 +10,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 namespace ccmc {
@@ -82,13 +83,33 @@ struct R4 {
     u64 v[4];
 };
 
-__device__ __forceinline__ R4 philox(u64 c0, u64 c1, u64 c2, u64 c3, u64 k0, u64 k1)
+// 64x64 -> 128-bit product (host builds: four 32x32 -> 64 multiply-adds):
+// x*m = p0 + 2^32 (xL mH + xH mL) + 2^64 xH mH; with t = xL mH + hi32(p0) and
+// u = xH mL + lo32(t) (neither overflows), lo = lo32(p0) | lo32(u) << 32 and
+// hi = xH mH + hi32(t) + hi32(u).
+__host__ __device__ __forceinline__ void mulhilo64(u64 x, u64 m, u64 &hi, u64 &lo)
+{
+#ifdef __CUDA_ARCH__
+    hi = __umul64hi(x, m);   // measured faster on sm_103a than the limb form below
+    lo = x * m;
+    return;
+#endif
+    const u64 xl = x & 0xFFFFFFFFULL, xh = x >> 32, ml = m & 0xFFFFFFFFULL, mh = m >> 32;
+    const u64 p0 = xl * ml;
+    const u64 t = xl * mh + (p0 >> 32);
+    const u64 u = xh * ml + (t & 0xFFFFFFFFULL);
+    hi = xh * mh + (t >> 32) + (u >> 32);
+    lo = (p0 & 0xFFFFFFFFULL) | (u << 32);
+}
+
+__host__ __device__ __forceinline__ R4 philox(u64 c0, u64 c1, u64 c2, u64 c3, u64 k0, u64 k1)
 {
 #pragma unroll
     for (int r = 0; r < 10; r++) {
         const u64 m0 = 0xD2E7470EE14C6C93ULL, m1 = 0xCA5A826395121157ULL;
-        u64 hi0 = __umul64hi(m0, c0), lo0 = m0 * c0;
-        u64 hi1 = __umul64hi(m1, c2), lo1 = m1 * c2;
+        u64 hi0, lo0, hi1, lo1;
+        mulhilo64(c0, m0, hi0, lo0);
+        mulhilo64(c2, m1, hi1, lo1);
         u64 n0 = hi1 ^ c1 ^ k0;
         u64 n2 = hi0 ^ c3 ^ k1;
         c0 = n0;
@@ -106,7 +127,7 @@ __device__ __forceinline__ R4 philox(u64 c0, u64 c1, u64 c2, u64 c3, u64 k0, u64
     return o;
 }
 
-__device__ __forceinline__ R4 draw(u64 k0, u64 k1, u64 it, u64 tag, u64 index, u64 block)
+__host__ __device__ __forceinline__ R4 draw(u64 k0, u64 k1, u64 it, u64 tag, u64 index, u64 block)
 {
     return philox(it, (tag << 56) | index, block, 0, k0, k1);
 }
@@ -655,6 +676,65 @@ __host__ __device__ __forceinline__ bool stoch_round_bits(u64 xbits, u64 r, cons
     }
     out = neg ? -n : n;
     return true;
+}
+
+// ---------------------------------------------------------------------------
+// Exact fixed-point accumulation of FP64 terms: each term is truncated to a
+// multiple of 2^-64 and summed as a 128-bit two's-complement integer, so the
+// sum is independent of the order of the terms and uses no FP64 operations.
+// ---------------------------------------------------------------------------
+
+struct Fix128 {
+    u64 lo, hi;
+    __host__ __device__ __forceinline__ void add(const Fix128 &b)
+    {
+        u64 l = lo + b.lo;
+        hi = hi + b.hi + (l < lo ? 1ULL : 0ULL);
+        lo = l;
+    }
+};
+
+__host__ __device__ __forceinline__ Fix128 to_fix(double x)
+{
+    u64 bits;
+    memcpy(&bits, &x, 8);
+    Fix128 r = {0, 0};
+    u64 ab = bits & 0x7FFFFFFFFFFFFFFFULL;
+    if (ab >= 0x43E0000000000000ULL) return r;   // |x| >= 2^63: out of range (not produced by the step)
+    u64 M;
+    int E;
+    split_double(ab, M, E);
+    int sft = E + 64;                            // value * 2^64 = M * 2^sft
+    if (sft >= 64) {
+        r.hi = M << (sft - 64);
+    } else if (sft > 0) {
+        r.lo = M << sft;
+        r.hi = M >> (64 - sft);
+    } else if (sft > -64) {
+        r.lo = M >> (-sft);
+    }
+    if (bits >> 63) {                            // negate
+        r.lo = ~r.lo;
+        r.hi = ~r.hi;
+        u64 l = r.lo + 1;
+        r.hi += (l == 0) ? 1ULL : 0ULL;
+        r.lo = l;
+    }
+    return r;
+}
+
+__host__ __device__ __forceinline__ double fix_to_double(Fix128 v)
+{
+    bool neg = (v.hi >> 63) != 0;
+    if (neg) {
+        v.lo = ~v.lo;
+        v.hi = ~v.hi;
+        u64 l = v.lo + 1;
+        v.hi += (l == 0) ? 1ULL : 0ULL;
+        v.lo = l;
+    }
+    double d = (double)v.hi + (double)v.lo * 0x1p-64;
+    return neg ? -d : d;
 }
 
 // ---------------------------------------------------------------------------

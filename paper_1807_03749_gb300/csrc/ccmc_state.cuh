@@ -96,7 +96,7 @@ struct WorkArrays {
     i64 *death;       // death deltas (fixed point)
     i64 *acc;         // reduced spawned weight matched to each list entry
     i64 *part;        // block partials of the scans (4 per block)
-    double *enum_part;  // (sum, compensation) per producing block
+    u64 *enum_part;   // 128-bit fixed-point E_num partial (lo, hi) per producing block
     i64 *newpop;      // list values after the merge (threshold applied)
     i64 *keep_l;      // keep flags of list entries -> exclusive prefix
     i64 *keep_s;      // keep flags of reduced spawns -> exclusive prefix

@@ -109,6 +109,40 @@ __device__ __forceinline__ KSum block_ksum(KSum k, double *sm)
     return r;
 }
 
+__device__ __forceinline__ Fix128 warp_fix(Fix128 v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Fix128 t;
+        t.lo = __shfl_xor_sync(FULLMASK, v.lo, o);
+        t.hi = __shfl_xor_sync(FULLMASK, v.hi, o);
+        v.add(t);
+    }
+    return v;
+}
+
+// integer block sum of Fix128 values; sm holds 64 u64; the result is valid in thread 0
+__device__ __forceinline__ Fix128 block_fix(Fix128 v, u64 *sm)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_fix(v);
+    if (lane == 0) {
+        sm[2 * wid] = v.lo;
+        sm[2 * wid + 1] = v.hi;
+    }
+    __syncthreads();
+    Fix128 r = {0, 0};
+    if (wid == 0) {
+        if (lane < nw) {
+            r.lo = sm[2 * lane];
+            r.hi = sm[2 * lane + 1];
+        }
+        r = warp_fix(r);
+    }
+    __syncthreads();
+    return r;
+}
+
 // contiguous share [lo, hi) of n elements for this block
 __device__ __forceinline__ void chunk_of(i64 n, i64 &lo, i64 &hi)
 {
@@ -406,13 +440,13 @@ template <int K>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(SysDev s, ListView L, DevStep *st, RunParams p, WorkArrays wa)
 {
     __shared__ i64 sm[32];
-    __shared__ double smd[64];
+    __shared__ u64 smf[64];
     i64 n = st->n_occ, lo, hi;
     chunk_of(n, lo, hi);
     i64 cw = wa.part[4 * blockIdx.x + 2], ca = wa.part[4 * blockIdx.x + 3];
     const u64 it = st->iter;
     const double S = st->shift;
-    KSum es = {0.0, 0.0};
+    Fix128 es = {0, 0};
     unsigned err = 0;
     for (i64 base = lo; base < hi; base += blockDim.x) {
         i64 i = base + threadIdx.x;
@@ -441,7 +475,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(SysDev s, ListView 
                 int sd = excitor_sign(s, d);
                 double coef = sd > 0 ? amp : -amp;
                 int lev = level_of(s, d);
-                if (lev == 1 || lev == 2) es.add(h_ref(s, d) * coef);
+                if (lev == 1 || lev == 2) es.add(to_fix(h_ref(s, d) * coef));
                 R4 r = draw(p.seed, p.replica, it, TAG_VISIT, (u64)i, 0);
                 double dE = i == 0 ? 0.0 : L.diag[i];
                 double x = (p.tau * (dE - S)) * coef;
@@ -454,10 +488,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(SysDev s, ListView 
         cw += tw;
         ca += ta;
     }
-    es = block_ksum(es, smd);
+    es = block_fix(es, smf);
     if (threadIdx.x == 0) {
-        wa.enum_part[2 * blockIdx.x] = es.s;
-        wa.enum_part[2 * blockIdx.x + 1] = es.c;
+        wa.enum_part[2 * blockIdx.x] = es.lo;
+        wa.enum_part[2 * blockIdx.x + 1] = es.hi;
         if (err) atomicOr(&st->err, err);
     }
 }
@@ -471,7 +505,7 @@ __global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(SysDev s, ListView L
                                                          SpawnBuf sp, ClusterBuf cl, int enum_base)
 {
     __shared__ double smag[8];
-    __shared__ double smd[64];
+    __shared__ u64 smf[64];
     __shared__ i64 sm[32];
     if (threadIdx.x < 8) smag[threadIdx.x] = st->mag[threadIdx.x];
     __syncthreads();
@@ -483,7 +517,7 @@ __global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(SysDev s, ListView L
     const int lane = threadIdx.x & 31;
     const i64 nwarps = (i64)gridDim.x * blockDim.x / 32;
     const i64 wglob = ((i64)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-    KSum es = {0.0, 0.0};
+    Fix128 es = {0, 0};
     unsigned err = 0;
     i64 inline_att = 0;
     for (i64 g0 = wglob * 32; g0 < n_sel; g0 += nwarps * 32) {
@@ -537,7 +571,7 @@ __global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(SysDev s, ListView L
             int lev = valid ? level_of(s, dj) : 0;
             if (valid && lev <= s.lmax + 2) {
                 double coef = (par & 1) ? -amp : amp;
-                if (lev == 1 || lev == 2) es.add(h_ref(s, dj) * coef);
+                if (lev == 1 || lev == 2) es.add(to_fix(h_ref(s, dj) * coef));
                 int sdj = excitor_sign(s, dj);
                 if (sz <= 1) {
                     double dE = sz == 0 ? 0.0 : L.diag[idx0];
@@ -601,11 +635,11 @@ __global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(SysDev s, ListView L
             }
         }
     }
-    es = block_ksum(es, smd);
+    es = block_fix(es, smf);
     inline_att = block_sum(inline_att, sm);
     if (threadIdx.x == 0) {
-        wa.enum_part[2 * (enum_base + blockIdx.x)] = es.s;
-        wa.enum_part[2 * (enum_base + blockIdx.x) + 1] = es.c;
+        wa.enum_part[2 * (enum_base + blockIdx.x)] = es.lo;
+        wa.enum_part[2 * (enum_base + blockIdx.x) + 1] = es.hi;
         if (inline_att) atomicAdd((unsigned long long *)&st->n_attempts, (unsigned long long)inline_att);
         if (err) atomicOr(&st->err, err);
     }
@@ -1014,13 +1048,13 @@ __global__ void __launch_bounds__(WORK_THREADS) k_scatter_new(SysDev s, ListView
 __global__ void __launch_bounds__(1024) k_finalize(DevStep *st, RunParams p, WorkArrays wa, ClusterBuf cl, int slots,
                                                    i64 list_cap)
 {
-    __shared__ double smd[64];
-    KSum k = {0.0, 0.0};
+    __shared__ u64 smf[64];
+    Fix128 k = {0, 0};
     for (int q = threadIdx.x; q < slots; q += blockDim.x) {
-        KSum t = {wa.enum_part[2 * q], wa.enum_part[2 * q + 1]};
-        k.merge(t);
+        Fix128 t = {wa.enum_part[2 * q], wa.enum_part[2 * q + 1]};
+        k.add(t);
     }
-    k = block_ksum(k, smd);
+    k = block_fix(k, smf);
     if (threadIdx.x == 0) {
         i64 ncl = (i64)(st->cl_packed >> CL_SHIFT);
         if (ncl > cl.cap) ncl = cl.cap;
@@ -1034,7 +1068,7 @@ __global__ void __launch_bounds__(1024) k_finalize(DevStep *st, RunParams p, Wor
         r.n_visit = p.fnc ? st->n_occ : 0;
         r.n_attempts = st->fnc_attempts + tc + st->n_attempts;
         r.n_spawned = st->n_sp;
-        r.e_num = k.s + k.c;
+        r.e_num = fix_to_double(k);
         r.ntot_after = st->ntot_after;
         r.nocc_after = st->kept_list + st->kept_new;
         r.n_keys = st->n_keys;
