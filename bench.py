@@ -161,6 +161,12 @@ def oracle_state(w):
     return sim, len(keys)
 
 
+def slices_for(sim, per_slice=200_000):
+    """Number of slices of a full step holding about per_slice samples each."""
+    r0 = sim.sample_range(0, 0, 0, 0)
+    return max(1, (r0.n_sel + r0.n_visit + per_slice - 1) // per_slice)
+
+
 def oracle_slices(sim, n_occ, nslices, count, it0=1500):
     """Times `count` slices, each 1/nslices of one full step's visits and
     cluster samples (propagation only).  Returns (samples, seconds, spawned)."""
@@ -187,7 +193,7 @@ def run_reference(args, w):
     if rank != 0:
         return
     sim, n_occ = oracle_state(w)
-    nslices = 20
+    nslices = slices_for(sim)
     oracle_slices(sim, n_occ, nslices, args.warmup)
     samples, secs, spawned = oracle_slices(sim, n_occ, nslices, args.steps)
     v = samples / secs
@@ -231,19 +237,39 @@ def run_gpu(args, w):
     ctx = ccmc.from_workload(w, replica=rank, stream=stream.cuda_stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
 
-    # growth to the target population (untimed)
+    # growth to the target population (untimed).  Large workloads grow at a
+    # fraction f of the target, then every population (reference included)
+    # is scaled by 1/f: t_HF exp(T/t_HF) scales as a whole, so this is the
+    # same wavefunction at the target population.
+    frac = float(w.get("grow_fraction", 1.0))
+    gctx = ctx if frac == 1.0 else ccmc.from_workload(w, replica=rank, stream=stream.cuda_stream,
+                                                      target_pop=w["target_pop"] * frac)
     t_grow = time.perf_counter()
     grown = 0
     reached = None
     while grown < args.grow_max:
-        ctx.step(w["shift_a"])
+        gctx.step(w["shift_a"])
         grown += w["shift_a"]
-        it, shift, vary, nprev = ctx.get_state()
+        it, shift, vary, nprev = gctx.get_state()
+        en = gctx.energy()
+        if en["n_total"] > 1e3 * max(en["n0"], 1.0) or time.perf_counter() - t_grow > args.grow_seconds:
+            raise RuntimeError(f"growth did not settle: N_total={en['n_total']:.3e}, t_HF={en['n0']:.3e} "
+                               f"after {grown} steps")
         if vary and reached is None:
             reached = grown
         if reached is not None and grown >= reached + args.equilibrate:
             break
-    ctx.sync()
+    gctx.sync()
+    state_note = f"grown from HF for {grown} steps"
+    if gctx is not ctx:
+        bits, _, pop = gctx.get_list()
+        it, shift, vary, nprev = gctx.get_state()
+        n_now = float(abs(pop).sum()) / 65536.0
+        scale = max(1, int(round(w["target_pop"] / n_now)))
+        ctx.set_list(bits, pop * scale)
+        ctx.set_state(it, shift, vary, nprev * scale)
+        del gctx
+        state_note += f" at {frac:g} of the target, populations then scaled x{scale}"
     t_grow = time.perf_counter() - t_grow
     ctx.records()
 
@@ -345,7 +371,7 @@ def run_gpu(args, w):
         "config": {"workload": w["name"], "electrons": w["nel"], "spin_orbitals": w["nso"], "truncation": w["lmax"],
                    "target_pop": w["target_pop"], "tau": w["tau"],
                    "sampling": "fnc+multispawn" if w["fnc"] else "original",
-                   "state": f"grown from HF for {grown} steps ({t_grow:.1f} s), shift varying",
+                   "state": f"{state_note} ({t_grow:.1f} s), shift varying",
                    "n_occ": recs[-1]["nocc_after"], "n_total": recs[-1]["ntot_after"] / 65536.0,
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas{world}"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -384,15 +410,12 @@ def cpu_baseline(w):
         sim, n_occ = oracle_state(w)
     except Exception as e:  # the oracle is a reported baseline only
         return {"value": None, "unit": "samples/s", "cores": 1, "kind": "oracle", "sample": f"unavailable: {e}"}
-    nslices = 20
-    samples, secs, done = 0, 0.0, 0
-    while secs < 8.0 and done < 4:
-        s, t, _ = oracle_slices(sim, n_occ, nslices, nslices, it0=1500 + done)
-        samples += s
-        secs += t
-        done += 1
+    nslices = slices_for(sim)
+    s1, t1, _ = oracle_slices(sim, n_occ, nslices, 1)          # calibration slice
+    done = max(1, min(4 * nslices, int(8.0 / max(t1, 1e-3))))
+    samples, secs, _ = oracle_slices(sim, n_occ, nslices, done)
     return {"value": samples / secs, "unit": "samples/s", "cores": 1, "kind": "oracle",
-            "sample": f"{done} full steps of visits + cluster samples (propagation only, in {nslices} slices each) "
+            "sample": f"{done} slice(s) of 1/{nslices} of a full step (visits + cluster samples, propagation only) "
                       f"on the oracle-made full-space state at N_total = target, {secs:.1f} s"}
 
 
@@ -405,15 +428,20 @@ def main():
     ap.add_argument("--workload", default="ueg14_m114_ccsdt_fnc_ms")
     ap.add_argument("--grow-max", type=int, default=8000)
     ap.add_argument("--equilibrate", type=int, default=100)
+    ap.add_argument("--grow-seconds", type=float, default=180.0)
     ap.add_argument("--profile-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--target-pop", type=float, default=0.0, help="override the workload's target population")
     ap.add_argument("--profile-window", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args()
     from ccmc_inputs import workload
 
-    w = workload(args.workload)
+    over = {}
+    if args.target_pop:
+        over["target_pop"] = args.target_pop   # smaller cases of a workload for profiling
+    w = workload(args.workload, **over)
     if args.impl == "reference":
         run_reference(args, w)
     else:

@@ -34,10 +34,14 @@ WORKLOADS = {
                                     tau=0.005, nsteps=2000, seed=1, fnc=True, multispawn=True),
     # synthetic molecule: 20 e in 41 spatial orbitals (82 spin-orbitals), CCSDTQ
     "mol20_m82_ccsdtq": dict(kind="generic", nel=20, norb=41, lmax=4, target_pop=1.0e7,
-                             tau=0.005, nsteps=50, seed=1, molecule_seed=7),
-    # UEG 54 e / 162 spin-orbitals (81 plane waves), CCSD, FP32 matrix elements
+                             tau=0.005, nsteps=50, seed=1, molecule_seed=7, grow_fraction=0.1),
+    # UEG 54 e / 162 spin-orbitals (81 plane waves), CCSD, FP32 matrix elements.
+    # 10^4 initial particles on HF: from 100 the original sampler stays below
+    # the shoulder on this system and the population blows up.  Grown at 1% of
+    # the target, then every population is scaled up to the target.
     "ueg54_m162_ccsd_fp32": dict(kind="ueg", nel=54, nso=162, rs=1.0, lmax=2, target_pop=1.0e8,
-                                 tau=0.01, nsteps=50, seed=1, precision="fp32"),
+                                 tau=0.01, nsteps=50, seed=1, precision="fp32", grow_fraction=0.01,
+                                 d0_init=1.0e4),
 }
 
 

@@ -98,6 +98,8 @@ def lib():
             "orc_ueg_tkin": (c_double, [c_void_p, c_int]),
             "orc_ueg_vq": (c_double, [c_void_p, c_int]),
             "orc_hij": (c_double, [c_void_p, u64p, u64p]),
+            "orc_hij_f": (c_double, [c_void_p, u64p, u64p]),
+            "orc_system_set_fp32": (c_int, [c_void_p]),
             "orc_hdiag_rel": (c_double, [c_void_p, u64p]),
             "orc_excitor_sign": (c_int, [c_void_p, u64p]),
             "orc_level": (c_int, [c_void_p, u64p]),
@@ -235,6 +237,19 @@ class System:
         b, bp = _u64(self.to_words(bra))
         k, kp = _u64(self.to_words(ket))
         return lib().orc_hij(self._h, bp, kp)
+
+    def hij_f(self, bra: int, ket: int) -> float:
+        """<bra|H|ket> of the FP32 form (after set_fp32)."""
+        b, bp = _u64(self.to_words(bra))
+        k, kp = _u64(self.to_words(ket))
+        return lib().orc_hij_f(self._h, bp, kp)
+
+    def set_fp32(self):
+        """Matrix elements and generation probabilities in single precision."""
+        if lib().orc_system_set_fp32(self._h):
+            raise MemoryError("orc_system_set_fp32 failed")
+        self.fp32 = True
+        return self
 
     def hdiag_rel(self, d: int) -> float:
         w, wp = _u64(self.to_words(d))

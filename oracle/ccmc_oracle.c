@@ -163,6 +163,12 @@ typedef struct {
     int no[2], nv[2];
     uint64_t ns, nd, ndcase[3];
     double inv_pgen_single[2], inv_pgen_double[3];
+    /* FP32 form: matrix elements and generation probabilities in single
+     * precision from tables rounded from the FP64 ones */
+    int fp32;
+    float *tkin_f, *vtab_f, *h1_f, *eri_f;
+    float ehf_rel_f;
+    float inv_pgen_ueg_f, inv_pgen_single_f[2], inv_pgen_double_f[3];
 } orc_system;
 
 static int spin_of(int p) { return p & 1; }
@@ -216,6 +222,7 @@ void orc_system_free(orc_system *s)
     if (!s) return;
     free(s->kv); free(s->grid); free(s->tkin); free(s->vtab);
     free(s->h1); free(s->eri);
+    free(s->tkin_f); free(s->vtab_f); free(s->h1_f); free(s->eri_f);
     free(s);
 }
 
@@ -419,6 +426,130 @@ double orc_hij(const orc_system *s, const uint64_t *bra_w, const uint64_t *ket_w
     double v2 = g2(s, a, b, j, i);
     double d = v1 - v2;
     return gamma > 0 ? d : -d;
+}
+
+/* ------------------------------------------------------------------------- */
+/* FP32 form of the same matrix elements (same operation order, float        */
+/* arithmetic on float tables).                                              */
+/* ------------------------------------------------------------------------- */
+
+static float eri_f_at(const orc_system *s, int p, int q, int r, int t)
+{
+    size_t n = (size_t)s->norb;
+    return s->eri_f[((p * n + q) * n + r) * n + t];
+}
+
+static float g2_f(const orc_system *s, int p, int q, int r, int t)
+{
+    if (spin_of(p) != spin_of(r) || spin_of(q) != spin_of(t)) return 0.0f;
+    if (s->kind == 0) {
+        const int *kp = s->kv[spat_of(p)], *kq = s->kv[spat_of(q)];
+        const int *kr = s->kv[spat_of(r)], *kt = s->kv[spat_of(t)];
+        for (int c = 0; c < 3; c++) if (kp[c] + kq[c] != kr[c] + kt[c]) return 0.0f;
+        return s->vtab_f[ueg_n2_between(s, p, r)];
+    }
+    return eri_f_at(s, spat_of(p), spat_of(r), spat_of(q), spat_of(t));
+}
+
+static float h_diag_abs_f(const orc_system *s, const det_t *d)
+{
+    int occ[64 * OW], n = 0;
+    for (int p = 0; p < s->nso; p++) if (det_bit(d, p)) occ[n++] = p;
+    if (s->kind == 0) {
+        float tsum = 0.0f, xsum = 0.0f;
+        for (int i = 0; i < n; i++) tsum = tsum + s->tkin_f[occ[i]];
+        for (int i = 0; i < n; i++)
+            for (int j = i + 1; j < n; j++)
+                if (spin_of(occ[i]) == spin_of(occ[j]))
+                    xsum = xsum + s->vtab_f[ueg_n2_between(s, occ[i], occ[j])];
+        return tsum - xsum;
+    }
+    float e1 = 0.0f, e2 = 0.0f;
+    for (int i = 0; i < n; i++) {
+        int P = spat_of(occ[i]);
+        e1 = e1 + s->h1_f[P * s->norb + P];
+    }
+    for (int i = 0; i < n; i++)
+        for (int j = i + 1; j < n; j++) {
+            int P = spat_of(occ[i]), Q = spat_of(occ[j]);
+            float t = eri_f_at(s, P, P, Q, Q);
+            if (spin_of(occ[i]) == spin_of(occ[j])) t = t - eri_f_at(s, P, Q, Q, P);
+            e2 = e2 + t;
+        }
+    return e1 + e2;
+}
+
+static float h_diag_rel_f(const orc_system *s, const det_t *d)
+{
+    return h_diag_abs_f(s, d) - s->ehf_rel_f;
+}
+
+/* <bra|H|ket> in single precision for bra != ket (0 for the diagonal). */
+static float hij_f(const orc_system *s, const det_t *bra, const det_t *ket)
+{
+    int holes[64 * OW], parts[64 * OW], nh = 0, np = 0;
+    for (int p = 0; p < s->nso; p++) {
+        int b = det_bit(bra, p), k = det_bit(ket, p);
+        if (k && !b) holes[nh++] = p;
+        if (b && !k) parts[np++] = p;
+    }
+    if (nh != np || nh == 0 || nh > 2) return 0.0f;
+    det_t cur = *ket;
+    int gamma = 1;
+    for (int m = 0; m < nh; m++) { gamma *= op_phase(&cur, holes[m]); det_clr(&cur, holes[m]); }
+    for (int m = np - 1; m >= 0; m--) { gamma *= op_phase(&cur, parts[m]); det_set(&cur, parts[m]); }
+    if (nh == 1) {
+        int i = holes[0], a = parts[0];
+        if (spin_of(i) != spin_of(a) || s->kind == 0) return 0.0f;
+        int A = spat_of(a), I = spat_of(i);
+        float acc = s->h1_f[A * s->norb + I];
+        for (int k = 0; k < s->nso; k++) {
+            if (!det_bit(ket, k) || k == i) continue;
+            int K = spat_of(k);
+            float t = eri_f_at(s, A, I, K, K);
+            if (spin_of(a) == spin_of(k)) t = t - eri_f_at(s, A, K, K, I);
+            acc = acc + t;
+        }
+        return gamma > 0 ? acc : -acc;
+    }
+    float v1 = g2_f(s, parts[0], parts[1], holes[0], holes[1]);
+    float v2 = g2_f(s, parts[0], parts[1], holes[1], holes[0]);
+    float d = v1 - v2;
+    return gamma > 0 ? d : -d;
+}
+
+/* Switch a system to the FP32 form. */
+int orc_system_set_fp32(orc_system *s)
+{
+    if (s->kind == 0) {
+        s->tkin_f = (float *)malloc(sizeof(float) * (size_t)s->nso);
+        s->vtab_f = (float *)malloc(sizeof(float) * (size_t)s->n2tab);
+        if (!s->tkin_f || !s->vtab_f) return ORC_ERR_OOM;
+        for (int p = 0; p < s->nso; p++) s->tkin_f[p] = (float)s->tkin[p];
+        for (int n2 = 0; n2 < s->n2tab; n2++) s->vtab_f[n2] = (float)s->vtab[n2];
+        s->inv_pgen_ueg_f = (float)s->inv_pgen_ueg;
+    } else {
+        size_t n2 = (size_t)s->norb * s->norb;
+        s->h1_f = (float *)malloc(sizeof(float) * n2);
+        s->eri_f = (float *)malloc(sizeof(float) * n2 * n2);
+        if (!s->h1_f || !s->eri_f) return ORC_ERR_OOM;
+        for (size_t i = 0; i < n2; i++) s->h1_f[i] = (float)s->h1[i];
+        for (size_t i = 0; i < n2 * n2; i++) s->eri_f[i] = (float)s->eri[i];
+        for (int g = 0; g < 2; g++) s->inv_pgen_single_f[g] = (float)s->inv_pgen_single[g];
+        for (int c = 0; c < 3; c++) s->inv_pgen_double_f[c] = (float)s->inv_pgen_double[c];
+    }
+    s->fp32 = 1;
+    s->ehf_rel_f = 0.0f;
+    s->ehf_rel_f = h_diag_abs_f(s, &s->hf);
+    return 0;
+}
+
+double orc_hij_f(const orc_system *s, const uint64_t *bra_w, const uint64_t *ket_w)
+{
+    det_t bra = {{0}}, ket = {{0}};
+    for (int i = 0; i < s->nw; i++) { bra.w[i] = bra_w[i]; ket.w[i] = ket_w[i]; }
+    if (det_equal(&bra, &ket, s->nw)) return (double)h_diag_abs_f(s, &ket);
+    return (double)hij_f(s, &bra, &ket);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -764,6 +895,27 @@ void orc_sim_free(orc_sim *m)
     free(m);
 }
 
+/* The FP32 counterpart of a generation probability (1/p_gen) of this system. */
+static float pgen_f_of(const orc_system *s, double inv_pgen)
+{
+    if (s->kind == 0) return s->inv_pgen_ueg_f;
+    for (int g = 0; g < 2; g++) if (inv_pgen == s->inv_pgen_single[g]) return s->inv_pgen_single_f[g];
+    for (int c = 0; c < 3; c++) if (inv_pgen == s->inv_pgen_double[c]) return s->inv_pgen_double_f[c];
+    return (float)inv_pgen;
+}
+
+/* Diagonal energy relative to HF in the system's precision. */
+static double diag_rel_p(const orc_system *s, const det_t *d)
+{
+    return s->fp32 ? (double)h_diag_rel_f(s, d) : h_diag_rel(s, d);
+}
+
+/* <HF|H|D> in the system's precision. */
+static double href_p(const orc_system *s, const det_t *d)
+{
+    return s->fp32 ? (double)hij_f(s, &s->hf, d) : orc_hij(s, s->hf.w, d->w);
+}
+
 /* Spawning attempts from one cluster, Sec. II and Sec. IV.C: each attempt
  * carries the cluster coefficient divided by n_attempts.  The spawned value
  * onto excitor i is -dtau H_ij C s_D(i) / p_gen. */
@@ -782,6 +934,10 @@ static int spawn_attempts(orc_sim *m, const det_t *dj, double coef, int64_t n_at
         m->rec.n_attempts++;
         if (!excite(s, dj, r, &di, &h, &inv_pgen)) continue;
         if (level_of(s, &di) > s->lmax) continue;
+        if (s->fp32) {
+            h = (double)hij_f(s, &di, dj);
+            inv_pgen = (double)pgen_f_of(s, inv_pgen);
+        }
         double x = ((m->prm.tau * h) * inv_pgen) * c_att;
         if (excitor_sign(s, &di) > 0) x = -x;
         int64_t v = stoch_round(x, unif(r[3]), m->prm.spawn_cutoff, &err);
@@ -862,17 +1018,17 @@ static int sample_cluster(orc_sim *m, uint64_t g, const int64_t *prefix, int64_t
     int lev = level_of(s, &dj);
     if (lev > s->lmax + 2) return 0;
     double coef = sigma > 0 ? amp : -amp;
-    if (lev == 1 || lev == 2) enum_add(m, orc_hij(s, s->hf.w, dj.w) * coef);
+    if (lev == 1 || lev == 2) enum_add(m, href_p(s, &dj) * coef);
     /* death */
     int err = 0;
     int sdj = excitor_sign(s, &dj);
     if (sz <= 1) {
-        double dE = (sz == 0) ? 0.0 : h_diag_rel(s, &dj);
+        double dE = (sz == 0) ? 0.0 : diag_rel_p(s, &dj);
         int64_t v = stoch_round(death_value(m, dE, coef, sdj), unif(r[1]), 0.0, &err);
         if (err) return err;
         m->death[idx[0]] += v;
     } else if (lev <= s->lmax) {
-        int64_t v = stoch_round(death_value(m, h_diag_rel(s, &dj), coef, sdj), unif(r[1]), 0.0, &err);
+        int64_t v = stoch_round(death_value(m, diag_rel_p(s, &dj), coef, sdj), unif(r[1]), 0.0, &err);
         if (err) return err;
         if (v != 0) {
             int rc = push_spawn(m, rank_key(s, &dj), v);
@@ -892,10 +1048,10 @@ static int visit_excitor(orc_sim *m, int64_t i)
     int sdj = excitor_sign(s, dj);
     double coef = sdj > 0 ? amp : -amp;
     int lev = level_of(s, dj);
-    if (lev == 1 || lev == 2) enum_add(m, orc_hij(s, s->hf.w, dj->w) * coef);
+    if (lev == 1 || lev == 2) enum_add(m, href_p(s, dj) * coef);
     uint64_t r[4];
     draw4(pkey, m->iter, TAG_VISIT, (uint64_t)i, 0, r);
-    double dE = (i == 0) ? 0.0 : h_diag_rel(s, dj);
+    double dE = (i == 0) ? 0.0 : diag_rel_p(s, dj);
     int err = 0;
     int64_t v = stoch_round(death_value(m, dE, coef, sdj), unif(r[0]), 0.0, &err);
     if (err) return err;

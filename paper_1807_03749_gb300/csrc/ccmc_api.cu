@@ -38,6 +38,9 @@ struct HostSys {
     u64 npairs = 0, nvirt = 0, ns = 0, nd = 0, ndcase[3] = {0, 0, 0};
     int no[2] = {0, 0}, nv[2] = {0, 0};
     double inv_pgen_ueg = 0.0, inv_pgen_single[2] = {0, 0}, inv_pgen_double[3] = {0, 0, 0};
+    // FP32 form
+    std::vector<float> tkin_f, vtab_f, h1_f, eri_f;
+    float ehf_rel_f = 0.0f;
 };
 
 void fill_binom(HostSys &h)
@@ -74,6 +77,38 @@ double host_diag(const HostSys &h, const std::vector<int> &occ)
             size_t P = occ[i] >> 1, Q = occ[j] >> 1;
             double t = h.eri[((P * no + P) * no + Q) * no + Q];
             if (((occ[i] ^ occ[j]) & 1) == 0) t = t - h.eri[((P * no + Q) * no + Q) * no + P];
+            e2 = e2 + t;
+        }
+    return e1 + e2;
+}
+
+// the same in single precision on the rounded tables (FP32 form)
+float host_diag_f(const HostSys &h, const std::vector<int> &occ)
+{
+    const int n = (int)occ.size();
+    if (h.kind == CCMC_UEG) {
+        float tsum = 0.0f, xsum = 0.0f;
+        for (int i = 0; i < n; i++) tsum = tsum + h.tkin_f[occ[i]];
+        for (int i = 0; i < n; i++)
+            for (int j = i + 1; j < n; j++)
+                if (((occ[i] ^ occ[j]) & 1) == 0) {
+                    const int *a = &h.kv[3 * (occ[i] >> 1)], *b = &h.kv[3 * (occ[j] >> 1)];
+                    int dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+                    xsum = xsum + h.vtab_f[dx * dx + dy * dy + dz * dz];
+                }
+        return tsum - xsum;
+    }
+    float e1 = 0.0f, e2 = 0.0f;
+    const size_t no = (size_t)h.norb;
+    for (int i = 0; i < n; i++) {
+        int P = occ[i] >> 1;
+        e1 = e1 + h.h1_f[P * no + P];
+    }
+    for (int i = 0; i < n; i++)
+        for (int j = i + 1; j < n; j++) {
+            size_t P = occ[i] >> 1, Q = occ[j] >> 1;
+            float t = h.eri_f[((P * no + P) * no + Q) * no + Q];
+            if (((occ[i] ^ occ[j]) & 1) == 0) t = t - h.eri_f[((P * no + Q) * no + Q) * no + P];
             e2 = e2 + t;
         }
     return e1 + e2;
@@ -212,24 +247,34 @@ ccmc_status status_from_bits(ccmc_ctx *ctx, unsigned bits)
 }
 
 // device helper kernels for list upload: keys and diagonal energies
-template <int K>
+template <int K, typename R>
 __global__ void k_prepare_list(SysDev s, ListView L, i64 n)
 {
     for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
         Det<K> d;
         for (int w = 0; w < K; w++) d.w[w] = L.bits[w * L.cap + i];
         L.key[i] = rank_key(s, d);
-        L.diag[i] = is_hf(s, d) ? 0.0 : diag_rel(s, d);
+        L.diag[i] = is_hf(s, d) ? 0.0 : diag_rel<K, R>(s, d);
     }
 }
 
 cudaError_t prepare_list(ccmc_ctx *ctx, ListView &L, i64 n)
 {
     int g = (int)std::min<i64>(4096, (n + 255) / 256 + 1);
+    const bool f = ctx->sc.fp32;
     switch (ctx->sc.K) {
-    case 1: k_prepare_list<1><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n); break;
-    case 2: k_prepare_list<2><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n); break;
-    default: k_prepare_list<3><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n); break;
+    case 1:
+        if (f) k_prepare_list<1, float><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n);
+        else k_prepare_list<1, double><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n);
+        break;
+    case 2:
+        if (f) k_prepare_list<2, float><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n);
+        else k_prepare_list<2, double><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n);
+        break;
+    default:
+        if (f) k_prepare_list<3, float><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n);
+        else k_prepare_list<3, double><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n);
+        break;
     }
     return cudaGetLastError();
 }
@@ -251,6 +296,7 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     if (!(params->tau > 0.0) || params->shift_a < 1 || !(params->d0_init > 0.0)) return CCMC_ERR_ARG;
     if (params->multispawn && !(params->a_thresh > 0.0)) return CCMC_ERR_ARG;
     if (params->radix_bits < 0 || params->radix_bits > MAX_DIGIT_BITS) return CCMC_ERR_ARG;
+    if (params->precision != CCMC_FP64 && params->precision != CCMC_FP32) return CCMC_ERR_ARG;
 
     ccmc_ctx *ctx = new (std::nothrow) ccmc_ctx();
     if (!ctx) return CCMC_ERR_OOM;
@@ -294,6 +340,12 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     std::vector<int> hfocc(nel);
     for (int p = 0; p < nel; p++) hfocc[p] = p;
     h.ehf_rel = host_diag(h, hfocc);
+    // FP32 tables: rounded from the FP64 ones
+    h.tkin_f.assign(h.tkin.begin(), h.tkin.end());
+    h.vtab_f.assign(h.vtab.begin(), h.vtab.end());
+    h.h1_f.assign(h.h1.begin(), h.h1.end());
+    h.eri_f.assign(h.eri.begin(), h.eri.end());
+    h.ehf_rel_f = host_diag_f(h, hfocc);
     h.npairs = (u64)nel * (u64)(nel - 1) / 2;
     h.nvirt = (u64)(nso - nel);
     if (h.kind == CCMC_UEG) {
@@ -319,7 +371,9 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     u64 key_bound = h.nvranks * h.cocc;
     ctx->list_cap = params->list_capacity ? (i64)params->list_capacity
                                           : (i64)std::min<double>((double)key_bound, 2.0 * tgt + 4096.0);
-    ctx->spawn_cap = params->spawn_capacity ? (i64)params->spawn_capacity : (i64)(8.0 * tgt + 65536.0);
+    // spawned records per step: about one per attempt; multi-spawn makes several attempts per cluster
+    const double per = params->multispawn ? 8.0 : (params->fnc ? 3.0 : 2.0);
+    ctx->spawn_cap = params->spawn_capacity ? (i64)params->spawn_capacity : (i64)(per * tgt + 65536.0);
     ctx->cl_cap = params->multispawn ? (i64)(3.0 * tgt + 65536.0) : 1;
     if (ctx->list_cap < 2 || ctx->spawn_cap < 1 || ctx->spawn_cap >= (i64)0xFFFFFFFFLL) {
         delete ctx;
@@ -383,6 +437,17 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     s.npairs = h.npairs;
     s.nvirt = h.nvirt;
     s.rank_tab = (const u64 *)upload(h.rank_tab.data(), h.rank_tab.size() * sizeof(u64));
+    if (h.kind == CCMC_UEG) {
+        s.tkin_f = (const float *)upload(h.tkin_f.data(), h.tkin_f.size() * sizeof(float));
+        s.vtab_f = (const float *)upload(h.vtab_f.data(), h.vtab_f.size() * sizeof(float));
+    } else {
+        s.h1_f = (const float *)upload(h.h1_f.data(), h.h1_f.size() * sizeof(float));
+        s.eri_f = (const float *)upload(h.eri_f.data(), h.eri_f.size() * sizeof(float));
+    }
+    s.ehf_rel_f = h.ehf_rel_f;
+    s.inv_pgen_ueg_f = (float)h.inv_pgen_ueg;
+    for (int g = 0; g < 2; g++) s.inv_pgen_single_f[g] = (float)h.inv_pgen_single[g];
+    for (int c = 0; c < 3; c++) s.inv_pgen_double_f[c] = (float)h.inv_pgen_double[c];
     s.cocc = h.cocc;
     s.ehf_rel = h.ehf_rel;
 
@@ -424,6 +489,7 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     sh.digit_bits = params->radix_bits ? params->radix_bits : MAX_DIGIT_BITS;
     sh.enum_slots = sh.scan_grid + sh.work_grid;
     ctx->sc.K = h.nw;
+    ctx->sc.fp32 = params->precision == CCMC_FP32;
 
     // lists
     const int K = h.nw;

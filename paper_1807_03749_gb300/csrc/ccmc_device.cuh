@@ -68,6 +68,29 @@ struct SysDev {
     const u64 *rank_tab;
     u64 cocc;
     double ehf_rel;      // <HF|H|HF> without the core constant
+    // FP32 form: tables rounded from the FP64 ones
+    const float *tkin_f, *vtab_f, *h1_f, *eri_f;
+    float ehf_rel_f;
+    float inv_pgen_ueg_f;
+    float inv_pgen_single_f[2];
+    float inv_pgen_double_f[3];
+};
+
+// table selection by real type
+template <typename R> struct Tab;
+template <> struct Tab<double> {
+    static __device__ __forceinline__ const double *tkin(const SysDev &s) { return s.tkin; }
+    static __device__ __forceinline__ const double *vtab(const SysDev &s) { return s.vtab; }
+    static __device__ __forceinline__ const double *h1(const SysDev &s) { return s.h1; }
+    static __device__ __forceinline__ const double *eri(const SysDev &s) { return s.eri; }
+    static __device__ __forceinline__ double ehf(const SysDev &s) { return s.ehf_rel; }
+};
+template <> struct Tab<float> {
+    static __device__ __forceinline__ const float *tkin(const SysDev &s) { return s.tkin_f; }
+    static __device__ __forceinline__ const float *vtab(const SysDev &s) { return s.vtab_f; }
+    static __device__ __forceinline__ const float *h1(const SysDev &s) { return s.h1_f; }
+    static __device__ __forceinline__ const float *eri(const SysDev &s) { return s.eri_f; }
+    static __device__ __forceinline__ float ehf(const SysDev &s) { return s.ehf_rel_f; }
 };
 
 template <int K>
@@ -359,24 +382,27 @@ __device__ __forceinline__ int ueg_n2(const SysDev &s, int p, int q)
     return dx * dx + dy * dy + dz * dz;
 }
 
-__device__ __forceinline__ double eri_at(const SysDev &s, int p, int q, int r, int t)
+template <typename R>
+__device__ __forceinline__ R eri_at(const SysDev &s, int p, int q, int r, int t)
 {
     size_t n = (size_t)s.norb;
-    return __ldg(&s.eri[((p * n + q) * n + r) * n + t]);
+    return __ldg(&Tab<R>::eri(s)[((p * n + q) * n + r) * n + t]);
 }
 
 // physicists' <pq|rs> for a momentum-conserving (UEG) or any (generic) quadruple
-__device__ __forceinline__ double g2(const SysDev &s, int p, int q, int r, int t)
+template <typename R>
+__device__ __forceinline__ R g2(const SysDev &s, int p, int q, int r, int t)
 {
-    if (((p ^ r) & 1) || ((q ^ t) & 1)) return 0.0;
-    if (s.kind == 0) return __ldg(&s.vtab[ueg_n2(s, p, r)]);
-    return eri_at(s, p >> 1, r >> 1, q >> 1, t >> 1);
+    if (((p ^ r) & 1) || ((q ^ t) & 1)) return R(0);
+    if (s.kind == 0) return __ldg(&Tab<R>::vtab(s)[ueg_n2(s, p, r)]);
+    return eri_at<R>(s, p >> 1, r >> 1, q >> 1, t >> 1);
 }
 
 // <D|H|D> without the core constant: one-body sum over occupied p ascending,
-// then the pair sum over p < q ascending (UEG: Tsum - Xsum; generic: e1 + e2).
-template <int K>
-__device__ double diag_abs(const SysDev &s, const Det<K> &d)
+// then the pair sum over p < q ascending (UEG: Tsum - Xsum; generic: e1 + e2),
+// in the arithmetic of R (double, or float for the FP32 form).
+template <int K, typename R>
+__device__ R diag_abs(const SysDev &s, const Det<K> &d)
 {
     int occ[64 * MAXK];
     int n = 0;
@@ -389,38 +415,41 @@ __device__ double diag_abs(const SysDev &s, const Det<K> &d)
         }
     }
     if (s.kind == 0) {
-        double tsum = 0.0, xsum = 0.0;
-        for (int i = 0; i < n; i++) tsum = tsum + __ldg(&s.tkin[occ[i]]);
+        const R *tk = Tab<R>::tkin(s), *vt = Tab<R>::vtab(s);
+        R tsum = R(0), xsum = R(0);
+        for (int i = 0; i < n; i++) tsum = tsum + __ldg(&tk[occ[i]]);
         for (int i = 0; i < n; i++)
             for (int j = i + 1; j < n; j++)
-                if (((occ[i] ^ occ[j]) & 1) == 0) xsum = xsum + __ldg(&s.vtab[ueg_n2(s, occ[i], occ[j])]);
+                if (((occ[i] ^ occ[j]) & 1) == 0) xsum = xsum + __ldg(&vt[ueg_n2(s, occ[i], occ[j])]);
         return tsum - xsum;
     }
-    double e1 = 0.0, e2 = 0.0;
+    const R *h1 = Tab<R>::h1(s);
+    R e1 = R(0), e2 = R(0);
     for (int i = 0; i < n; i++) {
         int P = occ[i] >> 1;
-        e1 = e1 + __ldg(&s.h1[P * s.norb + P]);
+        e1 = e1 + __ldg(&h1[P * s.norb + P]);
     }
     for (int i = 0; i < n; i++)
         for (int j = i + 1; j < n; j++) {
             int P = occ[i] >> 1, Q = occ[j] >> 1;
-            double t = eri_at(s, P, P, Q, Q);
-            if (((occ[i] ^ occ[j]) & 1) == 0) t = t - eri_at(s, P, Q, Q, P);
+            R t = eri_at<R>(s, P, P, Q, Q);
+            if (((occ[i] ^ occ[j]) & 1) == 0) t = t - eri_at<R>(s, P, Q, Q, P);
             e2 = e2 + t;
         }
     return e1 + e2;
 }
 
-template <int K>
+// H_DD - E_HF, promoted to double
+template <int K, typename R>
 __device__ __forceinline__ double diag_rel(const SysDev &s, const Det<K> &d)
 {
-    return diag_abs(s, d) - s.ehf_rel;
+    return (double)(diag_abs<K, R>(s, d) - Tab<R>::ehf(s));
 }
 
 // <bra|H|ket> for determinants differing by one or two spin-orbitals.
 // holes i<j are in ket only, particles a<b in bra only; gamma is the phase of
-// a+_a a+_b a_j a_i |ket> = gamma |bra>.
-template <int K>
+// a+_a a+_b a_j a_i |ket> = gamma |bra>.  Computed in R, returned as double.
+template <int K, typename R>
 __device__ double h_offdiag(const SysDev &s, const Det<K> &ket, int nh, int i, int j, int a, int b)
 {
     Det<K> cur = ket;
@@ -434,14 +463,14 @@ __device__ double h_offdiag(const SysDev &s, const Det<K> &ket, int nh, int i, i
     }
     par += count_below(cur, a);
     if (nh == 2) {
-        double v1 = g2(s, a, b, i, j);
-        double v2 = g2(s, a, b, j, i);
-        double d = v1 - v2;
-        return (par & 1) ? -d : d;
+        R v1 = g2<R>(s, a, b, i, j);
+        R v2 = g2<R>(s, a, b, j, i);
+        R d = v1 - v2;
+        return (double)((par & 1) ? -d : d);
     }
     if (s.kind == 0 || ((i ^ a) & 1)) return 0.0;
     int A = a >> 1, I = i >> 1;
-    double acc = __ldg(&s.h1[A * s.norb + I]);
+    R acc = __ldg(&Tab<R>::h1(s)[A * s.norb + I]);
 #pragma unroll
     for (int w = 0; w < K; w++) {
         u64 m = ket.w[w];
@@ -450,16 +479,16 @@ __device__ double h_offdiag(const SysDev &s, const Det<K> &ket, int nh, int i, i
             m &= m - 1;
             if (k == i) continue;
             int Kk = k >> 1;
-            double t = eri_at(s, A, I, Kk, Kk);
-            if (((a ^ k) & 1) == 0) t = t - eri_at(s, A, Kk, Kk, I);
+            R t = eri_at<R>(s, A, I, Kk, Kk);
+            if (((a ^ k) & 1) == 0) t = t - eri_at<R>(s, A, Kk, Kk, I);
             acc = acc + t;
         }
     }
-    return (par & 1) ? -acc : acc;
+    return (double)((par & 1) ? -acc : acc);
 }
 
 // <bra|H|ket> for bra != ket by at most two spin-orbitals (else 0)
-template <int K>
+template <int K, typename R>
 __device__ double h_between(const SysDev &s, const Det<K> &bra, const Det<K> &ket)
 {
     int hol[2], par[2], nh = 0, np = 0;
@@ -479,17 +508,17 @@ __device__ double h_between(const SysDev &s, const Det<K> &bra, const Det<K> &ke
         }
     }
     if (nh != np || nh == 0 || nh > 2) return 0.0;
-    return h_offdiag(s, ket, nh, hol[0], nh == 2 ? hol[1] : 0, par[0], nh == 2 ? par[1] : 0);
+    return h_offdiag<K, R>(s, ket, nh, hol[0], nh == 2 ? hol[1] : 0, par[0], nh == 2 ? par[1] : 0);
 }
 
 // <HF|H|D> for D at level 1 or 2
-template <int K>
+template <int K, typename R>
 __device__ __forceinline__ double h_ref(const SysDev &s, const Det<K> &d)
 {
     Det<K> hf;
 #pragma unroll
     for (int w = 0; w < K; w++) hf.w[w] = s.hf[w];
-    return h_between(s, hf, d);
+    return h_between<K, R>(s, hf, d);
 }
 
 // ---------------------------------------------------------------------------
@@ -512,7 +541,7 @@ __device__ __forceinline__ void pair_of(u64 idx, int &x, int &y)
 // number of holes nh and 1/p_gen.
 template <int K>
 __device__ bool excite(const SysDev &s, const Det<K> &dj, const R4 &r, Det<K> &di, int &nh, int &i, int &j,
-                       int &a, int &b, double &inv_pgen)
+                       int &a, int &b, double &inv_pgen, float &inv_pgen_f)
 {
     if (s.kind == 0) {
         int x, y;
@@ -537,6 +566,7 @@ __device__ bool excite(const SysDev &s, const Det<K> &dj, const R4 &r, Det<K> &d
         b = aa < bb ? bb : aa;
         nh = 2;
         inv_pgen = s.inv_pgen_ueg;
+        inv_pgen_f = s.inv_pgen_ueg_f;
     } else if (below(r.v[0], s.ns_nd) < s.ns) {
         i = kth_occupied(dj, (int)below(r.v[1], (u64)s.nel));
         int sg = i & 1;
@@ -546,6 +576,7 @@ __device__ bool excite(const SysDev &s, const Det<K> &dj, const R4 &r, Det<K> &d
         j = b = 0;
         nh = 1;
         inv_pgen = s.inv_pgen_single[sg];
+        inv_pgen_f = s.inv_pgen_single_f[sg];
     } else {
         int x, y;
         pair_of(below(r.v[1], s.npairs), x, y);
@@ -572,6 +603,7 @@ __device__ bool excite(const SysDev &s, const Det<K> &dj, const R4 &r, Det<K> &d
         b = aa < bb ? bb : aa;
         nh = 2;
         inv_pgen = s.inv_pgen_double[c];
+        inv_pgen_f = s.inv_pgen_double_f[c];
     }
     di = dj;
     flip(di, i);

@@ -119,6 +119,7 @@ struct Shapes {
 // Everything the step launcher needs.
 struct StepCtx {
     int K;
+    bool fp32;            // FP32 matrix elements and generation probabilities
     SysDev sys;
     RunParams prm;
     ListView list[2];

@@ -177,6 +177,20 @@ __device__ __forceinline__ u64 warp_reserve_u64(u64 *counter, u64 count)
     return base + incl - count;
 }
 
+// Every thread of the block calls; one atomic per block reserves the
+// block's total and each thread receives its exclusive offset.
+template <typename T>
+__device__ __forceinline__ T block_reserve(T *counter, T count, T *sm, T *sbase)
+{
+    T tot;
+    T incl = block_incl_scan(count, sm, tot);
+    if (threadIdx.x == 0) *sbase = tot ? (T)atomicAdd((unsigned long long *)counter, (unsigned long long)tot) : T(0);
+    __syncthreads();
+    T base = *sbase;
+    __syncthreads();
+    return base + incl - count;
+}
+
 template <int K>
 __device__ __forceinline__ Det<K> load_det(const u64 *bits, i64 cap, i64 i)
 {
@@ -311,17 +325,20 @@ __device__ __forceinline__ i64 lower_bound_key(const u64 *keys, i64 n, u64 k)
 
 // One spawning attempt from dj carrying coefficient c_att (Sec. II):
 // value -dtau H_ij c_att s_D(i) / p_gen, stochastically rounded.
-template <int K>
+template <int K, typename R>
 __device__ __forceinline__ bool spawn_attempt(const SysDev &s, const RunParams &p, const Det<K> &dj, double c_att,
                                               const R4 &r, u64 &key, i64 &val, unsigned &err)
 {
     Det<K> di;
     int nh, i, j, a, b;
     double inv_pgen;
-    if (!excite(s, dj, r, di, nh, i, j, a, b, inv_pgen)) return false;
+    float inv_pgen_f;
+    if (!excite(s, dj, r, di, nh, i, j, a, b, inv_pgen, inv_pgen_f)) return false;
     if (level_of(s, di) > s.lmax) return false;
-    double h = h_offdiag(s, dj, nh, i, j, a, b);
-    double x = ((p.tau * h) * inv_pgen) * c_att;
+    // matrix element and 1/p_gen in the precision R; the value itself in FP64
+    double h = h_offdiag<K, R>(s, dj, nh, i, j, a, b);
+    double ipg = sizeof(R) == 4 ? (double)inv_pgen_f : inv_pgen;
+    double x = ((p.tau * h) * ipg) * c_att;
     if (excitor_sign(s, di) > 0) x = -x;
     i64 v;
     if (!round_value(x, r.v[3], p, true, v)) {
@@ -392,8 +409,11 @@ __global__ void __launch_bounds__(1024) k_scan_top(ListView L, DevStep *st, RunP
         st->ntot = ntot;
         st->nex = tw;
         // selection buckets: the smallest power of two 2^k with N_ex <= 2^(k + bucket_bits)
+        // about two buckets per list entry (bounded by the bucket array)
+        int bb = 4;
+        while (bb < wa.bucket_bits && (1LL << bb) < 2 * st->n_occ) bb++;
         int k = 0;
-        while (k < 62 && ((u64)tw >> (k + wa.bucket_bits)) != 0) k++;
+        while (k < 62 && ((u64)tw >> (k + bb)) != 0) k++;
         st->bucket_shift = k;
         st->nbuckets = tw > 0 ? (i64)(((u64)tw + (1ULL << k) - 1) >> k) : 0;
         st->n_sel = n_sel;
@@ -436,7 +456,7 @@ __global__ void __launch_bounds__(1024) k_scan_top(ListView L, DevStep *st, RunP
 
 // prefix arrays; with full non-composite sampling also every visit's death,
 // estimator contribution and attempt coefficient (Sec. IV.B)
-template <int K>
+template <int K, typename R>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(SysDev s, ListView L, DevStep *st, RunParams p, WorkArrays wa)
 {
     __shared__ i64 sm[32];
@@ -475,7 +495,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(SysDev s, ListView 
                 int sd = excitor_sign(s, d);
                 double coef = sd > 0 ? amp : -amp;
                 int lev = level_of(s, d);
-                if (lev == 1 || lev == 2) es.add(to_fix(h_ref(s, d) * coef));
+                if (lev == 1 || lev == 2) es.add(to_fix(h_ref<K, R>(s, d) * coef));
                 R4 r = draw(p.seed, p.replica, it, TAG_VISIT, (u64)i, 0);
                 double dE = i == 0 ? 0.0 : L.diag[i];
                 double x = (p.tau * (dE - S)) * coef;
@@ -492,21 +512,24 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(SysDev s, ListView 
     if (threadIdx.x == 0) {
         wa.enum_part[2 * blockIdx.x] = es.lo;
         wa.enum_part[2 * blockIdx.x + 1] = es.hi;
-        if (err) atomicOr(&st->err, err);
     }
+    if (err) atomicOr(&st->err, err);   // every thread reports its own bits
 }
 
 // ---------------------------------------------------------------------------
 // a2-a5: cluster sampling (Sec. II; composites only with FNC, Sec. IV.B)
 // ---------------------------------------------------------------------------
 
-template <int K>
+template <int K, typename R>
 __global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(SysDev s, ListView L, DevStep *st, RunParams p, WorkArrays wa,
                                                          SpawnBuf sp, ClusterBuf cl, int enum_base)
 {
     __shared__ double smag[8];
     __shared__ u64 smf[64];
     __shared__ i64 sm[32];
+    __shared__ u64 smu[32];
+    __shared__ i64 s_base;
+    __shared__ u64 s_ubase;
     if (threadIdx.x < 8) smag[threadIdx.x] = st->mag[threadIdx.x];
     __syncthreads();
     const i64 n_sel = st->n_sel, n = st->n_occ, nex = st->nex, n0 = st->n0;
@@ -514,14 +537,13 @@ __global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(SysDev s, ListView L
     const i64 nbk = st->nbuckets;
     const u64 it = st->iter;
     const double S = st->shift;
-    const int lane = threadIdx.x & 31;
-    const i64 nwarps = (i64)gridDim.x * blockDim.x / 32;
-    const i64 wglob = ((i64)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     Fix128 es = {0, 0};
     unsigned err = 0;
     i64 inline_att = 0;
-    for (i64 g0 = wglob * 32; g0 < n_sel; g0 += nwarps * 32) {
-        const i64 g = g0 + lane;
+    i64 death_hf = 0;   // reference-cluster deaths, summed per block at the end
+    // block-uniform loop: appends are reserved with one atomic per block
+    for (i64 g0 = (i64)blockIdx.x * blockDim.x; g0 < n_sel; g0 += (i64)gridDim.x * blockDim.x) {
+        const i64 g = g0 + threadIdx.x;
         int nrec = 0;
         u64 rk[2] = {0, 0};
         i64 rv[2] = {0, 0};
@@ -571,7 +593,7 @@ __global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(SysDev s, ListView L
             int lev = valid ? level_of(s, dj) : 0;
             if (valid && lev <= s.lmax + 2) {
                 double coef = (par & 1) ? -amp : amp;
-                if (lev == 1 || lev == 2) es.add(to_fix(h_ref(s, dj) * coef));
+                if (lev == 1 || lev == 2) es.add(to_fix(h_ref<K, R>(s, dj) * coef));
                 int sdj = excitor_sign(s, dj);
                 if (sz <= 1) {
                     double dE = sz == 0 ? 0.0 : L.diag[idx0];
@@ -579,9 +601,12 @@ __global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(SysDev s, ListView L
                     if (sdj > 0) x = -x;
                     i64 dv;
                     if (!round_value(x, r0.v[1], p, false, dv)) err |= ERRB_NUMERIC;
-                    if (dv != 0) atomicAdd((unsigned long long *)&wa.death[idx0], (unsigned long long)dv);
+                    if (dv != 0) {
+                        if (idx0 == 0) death_hf += dv;   // hot entry: one atomic per block below
+                        else atomicAdd((unsigned long long *)&wa.death[idx0], (unsigned long long)dv);
+                    }
                 } else if (lev <= s.lmax) {
-                    double x = (p.tau * (diag_rel(s, dj) - S)) * coef;
+                    double x = (p.tau * (diag_rel<K, R>(s, dj) - S)) * coef;
                     if (sdj > 0) x = -x;
                     i64 dv;
                     if (!round_value(x, r0.v[1], p, false, dv)) err |= ERRB_NUMERIC;
@@ -600,7 +625,7 @@ __global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(SysDev s, ListView L
                     R4 ra = draw(p.seed, p.replica, it, TAG_SAMPLE_ATT, (u64)g, 0);
                     u64 k;
                     i64 v;
-                    if (spawn_attempt(s, p, dj, coef, ra, k, v, err)) {
+                    if (spawn_attempt<K, R>(s, p, dj, coef, ra, k, v, err)) {
                         rk[nrec] = k;
                         rv[nrec] = v;
                         nrec++;
@@ -609,7 +634,7 @@ __global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(SysDev s, ListView L
             }
         }
         // convergent appends
-        i64 off = warp_reserve(&st->n_sp, nrec);
+        i64 off = block_reserve<i64>(&st->n_sp, (i64)nrec, sm, &s_base);
         for (int q = 0; q < nrec; q++) {
             if (off + q < sp.cap) {
                 sp.key[0][off + q] = rk[q];
@@ -620,7 +645,7 @@ __global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(SysDev s, ListView L
         }
         if (p.multispawn) {
             u64 mine = push ? ((1ULL << CL_SHIFT) | (u64)natt) : 0ULL;
-            u64 o = warp_reserve_u64(&st->cl_packed, mine);
+            u64 o = block_reserve<u64>(&st->cl_packed, mine, smu, &s_ubase);
             if (push) {
                 i64 c = (i64)(o >> CL_SHIFT);
                 i64 a0 = (i64)(o & CL_MASK);
@@ -637,12 +662,14 @@ __global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(SysDev s, ListView L
     }
     es = block_fix(es, smf);
     inline_att = block_sum(inline_att, sm);
+    death_hf = block_sum(death_hf, sm);
     if (threadIdx.x == 0) {
+        if (death_hf) atomicAdd((unsigned long long *)&wa.death[0], (unsigned long long)death_hf);
         wa.enum_part[2 * (enum_base + blockIdx.x)] = es.lo;
         wa.enum_part[2 * (enum_base + blockIdx.x) + 1] = es.hi;
         if (inline_att) atomicAdd((unsigned long long *)&st->n_attempts, (unsigned long long)inline_att);
-        if (err) atomicOr(&st->err, err);
     }
+    if (err) atomicOr(&st->err, err);   // every thread reports its own bits
 }
 
 // ---------------------------------------------------------------------------
@@ -650,7 +677,7 @@ __global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(SysDev s, ListView L
 // buffered composite clusters (Sec. IV.B-C)
 // ---------------------------------------------------------------------------
 
-template <int K>
+template <int K, typename R>
 __global__ void __launch_bounds__(WORK_THREADS, 4) k_attempts(SysDev s, ListView L, DevStep *st, RunParams p,
                                                               WorkArrays wa, SpawnBuf sp, ClusterBuf cl)
 {
@@ -695,7 +722,7 @@ __global__ void __launch_bounds__(WORK_THREADS, 4) k_attempts(SysDev s, ListView
                     idx = cl.index[o];
                 }
                 R4 r = draw(p.seed, p.replica, it, tag, idx, (u64)m);
-                if (spawn_attempt(s, p, dj, ca, r, k, v, err)) nrec = 1;
+                if (spawn_attempt<K, R>(s, p, dj, ca, r, k, v, err)) nrec = 1;
             }
             i64 off = warp_reserve(&st->n_sp, nrec);
             if (nrec) {
@@ -1005,11 +1032,11 @@ __global__ void __launch_bounds__(WORK_THREADS) k_scatter_list(SysDev s, ListVie
     asum = block_sum(asum, sm);
     if (threadIdx.x == 0) {
         if (asum) atomicAdd((unsigned long long *)&st->ntot_after, (unsigned long long)asum);
-        if (err) atomicOr(&st->err, err);
     }
+    if (err) atomicOr(&st->err, err);   // every thread reports its own bits
 }
 
-template <int K>
+template <int K, typename R>
 __global__ void __launch_bounds__(WORK_THREADS) k_scatter_new(SysDev s, ListView O, DevStep *st, WorkArrays wa,
                                                                const u64 *rkey, const i64 *rpop)
 {
@@ -1031,14 +1058,14 @@ __global__ void __launch_bounds__(WORK_THREADS) k_scatter_new(SysDev s, ListView
         store_det<K>(O.bits, O.cap, out, d);
         O.key[out] = k;
         O.pop[out] = v;
-        O.diag[out] = diag_rel(s, d);
+        O.diag[out] = diag_rel<K, R>(s, d);
         asum += v < 0 ? -v : v;
     }
     asum = block_sum(asum, sm);
     if (threadIdx.x == 0) {
         if (asum) atomicAdd((unsigned long long *)&st->ntot_after, (unsigned long long)asum);
-        if (err) atomicOr(&st->err, err);
     }
+    if (err) atomicOr(&st->err, err);   // every thread reports its own bits
 }
 
 // ---------------------------------------------------------------------------
@@ -1090,7 +1117,7 @@ int bits_for(u64 bound)
     return b;
 }
 
-template <int K>
+template <int K, typename R>
 static cudaError_t launch_step_k(StepCtx &c)
 {
     cudaStream_t sm = c.stream;
@@ -1106,16 +1133,16 @@ static cudaError_t launch_step_k(StepCtx &c)
     mark(0);
     k_scan_partial<<<sh.scan_grid, SCAN_THREADS, 0, sm>>>(L, c.st, c.prm, wa);
     k_scan_top<<<1, 1024, 0, sm>>>(L, c.st, c.prm, wa, sh.scan_grid, c.sys.lmax);
-    k_scan_final<K><<<sh.scan_grid, SCAN_THREADS, 0, sm>>>(c.sys, L, c.st, c.prm, wa);
+    k_scan_final<K, R><<<sh.scan_grid, SCAN_THREADS, 0, sm>>>(c.sys, L, c.st, c.prm, wa);
     c.launches[0] += 3;
     // a2-a5
     mark(1);
-    k_sample<K><<<sh.work_grid, WORK_THREADS, 0, sm>>>(c.sys, L, c.st, c.prm, wa, c.sp, c.cl, sh.scan_grid);
+    k_sample<K, R><<<sh.work_grid, WORK_THREADS, 0, sm>>>(c.sys, L, c.st, c.prm, wa, c.sp, c.cl, sh.scan_grid);
     c.launches[1] += 1;
     // a4/a6
     mark(2);
     if (c.prm.fnc || c.prm.multispawn) {
-        k_attempts<K><<<sh.work_grid, WORK_THREADS, 0, sm>>>(c.sys, L, c.st, c.prm, wa, c.sp, c.cl);
+        k_attempts<K, R><<<sh.work_grid, WORK_THREADS, 0, sm>>>(c.sys, L, c.st, c.prm, wa, c.sp, c.cl);
         c.launches[2] += 1;
     }
     // a7: radix sort of the spawned records
@@ -1152,7 +1179,7 @@ static cudaError_t launch_step_k(StepCtx &c)
     k_keep_top<<<1, 1024, 0, sm>>>(c.st, wa, sh.scan_grid);
     k_keep_final<<<2 * sh.scan_grid, SCAN_THREADS, 0, sm>>>(c.st, wa, sh.scan_grid);
     k_scatter_list<K><<<sh.work_grid, WORK_THREADS, 0, sm>>>(c.sys, L, O, c.st, wa, rkey);
-    k_scatter_new<K><<<sh.work_grid, WORK_THREADS, 0, sm>>>(c.sys, O, c.st, wa, rkey, rpop);
+    k_scatter_new<K, R><<<sh.work_grid, WORK_THREADS, 0, sm>>>(c.sys, O, c.st, wa, rkey, rpop);
     c.launches[5] += 7;
 
     // a10
@@ -1166,10 +1193,18 @@ static cudaError_t launch_step_k(StepCtx &c)
 
 cudaError_t launch_step(StepCtx &c)
 {
+    if (c.fp32) {
+        switch (c.K) {
+        case 1: return launch_step_k<1, float>(c);
+        case 2: return launch_step_k<2, float>(c);
+        case 3: return launch_step_k<3, float>(c);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (c.K) {
-    case 1: return launch_step_k<1>(c);
-    case 2: return launch_step_k<2>(c);
-    case 3: return launch_step_k<3>(c);
+    case 1: return launch_step_k<1, double>(c);
+    case 2: return launch_step_k<2, double>(c);
+    case 3: return launch_step_k<3, double>(c);
     default: return cudaErrorInvalidValue;
     }
 }

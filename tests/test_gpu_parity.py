@@ -30,8 +30,12 @@ def ccmc():
 
 def _oracle_system(w):
     if w["kind"] == "ueg":
-        return oracle.System.ueg(w["nel"], w["nso"], w["rs"], w["lmax"])
-    return oracle.System.generic(w["nel"], w["h1"], w["eri"], w["lmax"])
+        s = oracle.System.ueg(w["nel"], w["nso"], w["rs"], w["lmax"])
+    else:
+        s = oracle.System.generic(w["nel"], w["h1"], w["eri"], w["lmax"])
+    if w.get("precision") == "fp32":
+        s.set_fp32()
+    return s
 
 
 def _pair(ccmc, w, **over):
@@ -177,6 +181,46 @@ def test_three_word_determinants_bitexact(ccmc):
     w = workload("ueg54_m162_ccsd_fp32", precision="fp64", target_pop=1e5, d0_init=200.0)
     so, sim, ctx = _pair(ccmc, w)
     _run_lockstep(sim, ctx, 25, check_spawned_every=5)
+
+
+def test_fp32_form_ueg38_bitexact(ccmc):
+    """FP32 matrix elements (original sampling): the 200-step run in lockstep
+    with the oracle's FP32 form."""
+    w = workload("ueg14_m38_ccsd", precision="fp32")
+    so, sim, ctx = _pair(ccmc, w)
+    _run_lockstep(sim, ctx, 200, check_spawned_every=25)
+
+
+def test_fp32_form_three_words_and_molecule_bitexact(ccmc):
+    w = workload("ueg54_m162_ccsd_fp32", target_pop=1e5, d0_init=200.0)
+    so, sim, ctx = _pair(ccmc, w)
+    _run_lockstep(sim, ctx, 25, check_spawned_every=5)
+    h1, eri = molecule_integrals(norb=8, nocc=3, seed=5, scale=0.1)
+    wm = dict(kind="generic", nel=6, norb=8, nso=16, lmax=3, h1=h1, eri=eri, tau=0.01, target_pop=3000.0,
+              d0_init=400.0, shift_a=10, zeta=0.05, spawn_cutoff=2.0 ** -7, a_thresh=1.0, seed=3, replica=0,
+              fnc=1, multispawn=1, precision="fp32")
+    so, sim, ctx = _pair(ccmc, wm)
+    _run_lockstep(sim, ctx, 60, check_spawned_every=20)
+
+
+def test_fp32_estimator_accuracy_on_one_state(ccmc):
+    """From the same state both precisions draw the same clusters, so the
+    projected-energy numerators differ only by the FP32 matrix elements."""
+    w = workload("ueg14_m38_ccsd")
+    so, sim, ctx = _pair(ccmc, w)
+    sim.run(150)
+    bits, keys, pops = sim.get_list()
+    st = sim.get_state()
+    c64 = ccmc.from_workload(w)
+    c32 = ccmc.from_workload(w, precision="fp32")
+    e = []
+    for c in (c64, c32):
+        c.set_list(bits, pops)
+        c.set_state(*st)
+        c.step(1)
+        e.append(c.records()[-1]["e_num"])
+    rel = abs(e[1] - e[0]) / abs(e[0])
+    assert 0.0 < rel < 1e-5
 
 
 def test_negative_reference_weight(ccmc):
