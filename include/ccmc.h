@@ -110,8 +110,12 @@ typedef struct {
     ccmc_free_fn free;
     void *alloc_user;
     int32_t radix_bits;      /* digit width of the radix sort, 0 = default */
-    int32_t reserved;
+    int32_t flags;           /* CCMC_NO_GRAPH: launch kernels one by one instead of
+                                replaying a captured CUDA graph of the step */
 } ccmc_params;
+
+/* ccmc_params.flags */
+#define CCMC_NO_GRAPH 1
 
 /* Per-step record; one is kept for every step in a device ring buffer. */
 typedef struct {
@@ -140,6 +144,9 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
 /* Issues nsteps time steps (Sec. II) on the context's stream.  The host
  * synchronises only at shift-update boundaries (every shift_a steps) to take
  * the logarithm of the population ratio; otherwise the call is asynchronous.
+ * On a non-NULL stream the step's kernels are captured once into a CUDA graph
+ * and replayed (unless CCMC_NO_GRAPH or profiling is set); the first step of
+ * a context should therefore not be issued inside another stream capture.
  * Kernel-detected errors are returned by the first synchronising call. */
 ccmc_status ccmc_step(ccmc_ctx *ctx, int nsteps);
 

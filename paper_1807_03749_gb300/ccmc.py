@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
                 ("precision", c_int32), ("a_thresh", c_double), ("seed", c_uint64), ("replica", c_uint64),
                 ("list_capacity", c_uint64), ("spawn_capacity", c_uint64), ("cuda_stream", c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", c_void_p), ("radix_bits", c_int32),
-                ("reserved", c_int32)]
+                ("flags", c_int32)]
 
 
 class Record(ctypes.Structure):
@@ -140,7 +140,7 @@ class Context:
                  shift_a: int = 10, zeta: float = 0.05, spawn_cutoff: float = 2.0 ** -7, fnc: bool = False,
                  multispawn: bool = False, a_thresh: float = 1.0, seed: int = 1, replica: int = 0,
                  precision: str = "fp64", list_capacity: int = 0, spawn_capacity: int = 0, stream=None,
-                 use_torch_allocator: bool = False, radix_bits: int = 0, **_ignored):
+                 use_torch_allocator: bool = False, radix_bits: int = 0, use_graph: bool = True, **_ignored):
         L = load()
         self._lib = L
         self.nel, self.nso, self.lmax = nel, nso, lmax
@@ -166,6 +166,7 @@ class Context:
         p.seed, p.replica = seed, replica
         p.list_capacity, p.spawn_capacity = list_capacity, spawn_capacity
         p.radix_bits = radix_bits
+        p.flags = 0 if use_graph else 1
         if stream is not None:
             p.cuda_stream = c_void_p(int(stream))
         if use_torch_allocator:

@@ -216,6 +216,9 @@ struct ccmc_ctx {
     i64 list_cap = 0, spawn_cap = 0, cl_cap = 0;
     double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     i64 phase_launch0[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // captured CUDA graph of one step (replayed on non-NULL streams)
+    cudaGraphExec_t graph = nullptr;
+    i64 graph_launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -533,6 +536,7 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     wa.hist_tot = al.arr<unsigned>((size_t)(1 << MAX_DIGIT_BITS));
     wa.ring = al.arr<Record>(RING);
     ctx->sc.st = al.arr<DevStep>(1);
+    ctx->sc.d_args = al.arr<StepArgs>(1);
     if (al.failed) {
         al.release();
         delete ctx;
@@ -547,6 +551,22 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     ctx->sc.stream = ctx->stream;
     ctx->sc.cur = 0;
     ctx->sc.sorted_buf = 0;
+    {
+        StepArgs &ha = ctx->sc.h_args;
+        ha.s = ctx->sc.sys;
+        ha.p = ctx->sc.prm;
+        ha.list[0] = ctx->sc.list[0];
+        ha.list[1] = ctx->sc.list[1];
+        ha.sp = ctx->sc.sp;
+        ha.cl = ctx->sc.cl;
+        ha.wa = ctx->sc.wa;
+        ha.st = ctx->sc.st;
+        if (cudaMemcpy(ctx->sc.d_args, &ha, sizeof(StepArgs), cudaMemcpyHostToDevice) != cudaSuccess) {
+            al.release();
+            delete ctx;
+            return CCMC_ERR_CUDA;
+        }
+    }
     ctx->sc.profile = false;
     for (int e = 0; e < 8; e++) {
         ctx->sc.launches[e] = 0;
@@ -611,6 +631,7 @@ ccmc_status ccmc_set_list(ccmc_ctx *ctx, const uint64_t *bits, const int64_t *po
     st.iter = ctx->iter;
     st.shift = ctx->shift;
     st.n_occ = (i64)n;
+    st.cur = ctx->sc.cur;
     CK(cudaMemcpy(ctx->sc.st, &st, sizeof(DevStep), cudaMemcpyHostToDevice));
     ctx->stepped = false;
     return CCMC_OK;
@@ -623,12 +644,47 @@ static ccmc_status check_device(ccmc_ctx *ctx)
     return status_from_bits(ctx, ctx->h_st->err);
 }
 
+// One step: replay of the captured graph when possible, else kernel launches.
+static cudaError_t issue_step(ccmc_ctx *ctx)
+{
+    StepCtx &c = ctx->sc;
+    const bool use_graph = ctx->stream != nullptr && !c.profile && !(ctx->prm.flags & CCMC_NO_GRAPH);
+    if (!use_graph) return launch_step(c);
+    if (!ctx->graph) {
+        i64 before[8];
+        for (int i = 0; i < 8; i++) before[i] = c.launches[i];
+        int cur = c.cur;
+        cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        e = launch_step(c);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        for (int i = 0; i < 8; i++) {
+            ctx->graph_launches[i] = c.launches[i] - before[i];
+            c.launches[i] = before[i];
+        }
+        c.cur = cur;
+        if (e != cudaSuccess) {
+            ctx->graph = nullptr;
+            return e;
+        }
+    }
+    cudaError_t e = cudaGraphLaunch(ctx->graph, ctx->stream);
+    for (int i = 0; i < 8; i++) c.launches[i] += ctx->graph_launches[i];
+    c.sorted_buf = sort_passes(c.sh) & 1;
+    c.cur ^= 1;
+    return e;
+}
+
 ccmc_status ccmc_step(ccmc_ctx *ctx, int nsteps)
 {
     if (!ctx || nsteps < 0) return CCMC_ERR_ARG;
     const int A = ctx->prm.shift_a;
     for (int k = 0; k < nsteps; k++) {
-        cudaError_t e = launch_step(ctx->sc);
+        cudaError_t e = issue_step(ctx);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "launch_step");
         ctx->stepped = true;
         if (ctx->sc.profile) {
@@ -899,6 +955,7 @@ void ccmc_free(ccmc_ctx *ctx)
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     ctx->al.release();
     for (int e = 0; e < 8; e++)
         if (ctx->sc.events[e]) cudaEventDestroy(ctx->sc.events[e]);

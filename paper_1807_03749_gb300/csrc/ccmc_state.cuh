@@ -67,7 +67,7 @@ struct DevStep {
     i64 ntot_after;
     i64 n_start;        // list size at the start of the latest finished step
     unsigned err;
-    unsigned pad;
+    int cur;            // list buffer holding the current list
 };
 
 // Spawn buffer pair for the radix sort (ping-pong).
@@ -116,6 +116,18 @@ struct Shapes {
     int enum_slots;   // scan_grid + 2 * work_grid
 };
 
+// Per-replica arguments of the step kernels (device-resident; a single
+// context has one, a batch an array indexed by blockIdx.y).
+struct StepArgs {
+    SysDev s;
+    RunParams p;
+    ListView list[2];
+    SpawnBuf sp;
+    ClusterBuf cl;
+    WorkArrays wa;
+    DevStep *st;
+};
+
 // Everything the step launcher needs.
 struct StepCtx {
     int K;
@@ -136,12 +148,22 @@ struct StepCtx {
     cudaEvent_t events[8];
     i64 launches[8];      // kernels launched per phase (cumulative)
     i64 total_launches;
+    StepArgs h_args;      // host copy of this context's kernel arguments
+    StepArgs *d_args;     // device copy
 };
 
 constexpr int NPHASES = 7;
 
 // Issues one full time step on ctx.stream.  Returns a CUDA error code.
 cudaError_t launch_step(StepCtx &ctx);
+
+// Issues one step for nrep replicas of the same word count and precision
+// whose arguments are A[0..nrep); launch counts are added to launches[7].
+cudaError_t launch_group(const StepArgs *A, int nrep, int K, bool fp32, const Shapes &sh, bool multi_att,
+                         cudaStream_t sm, i64 *launches, const cudaEvent_t *ev);
+
+// Number of radix passes for the shapes.
+int sort_passes(const Shapes &sh);
 
 // Copies the rank-key bit count needed for a key bound.
 int bits_for(u64 bound);

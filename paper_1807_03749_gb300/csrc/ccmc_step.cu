@@ -367,7 +367,7 @@ __device__ __forceinline__ i64 threshold(const RunParams &p, u64 it, u64 key, i6
 // a1: scans over the list
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_partial(ListView L, DevStep *st, RunParams p, WorkArrays wa)
+__device__ __forceinline__ void d_scan_partial(const ListView &L, DevStep *st, const RunParams &p, const WorkArrays &wa)
 {
     __shared__ i64 sm[32];
     i64 n = st->n_occ, lo, hi;
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_partial(ListView L, DevSt
 }
 
 // one block of 1024 threads; grid <= 1024 partials
-__global__ void __launch_bounds__(1024) k_scan_top(ListView L, DevStep *st, RunParams p, WorkArrays wa, int grid, int lmax)
+__device__ __forceinline__ void d_scan_top(const ListView &L, DevStep *st, const RunParams &p, const WorkArrays &wa, int grid, int lmax)
 {
     __shared__ i64 sm[32];
     int t = threadIdx.x;
@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(1024) k_scan_top(ListView L, DevStep *st, RunP
 // prefix arrays; with full non-composite sampling also every visit's death,
 // estimator contribution and attempt coefficient (Sec. IV.B)
 template <int K, typename R>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(SysDev s, ListView L, DevStep *st, RunParams p, WorkArrays wa)
+__device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L, DevStep *st, const RunParams &p, const WorkArrays &wa)
 {
     __shared__ i64 sm[32];
     __shared__ u64 smf[64];
@@ -521,8 +521,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(SysDev s, ListView 
 // ---------------------------------------------------------------------------
 
 template <int K, typename R>
-__global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(SysDev s, ListView L, DevStep *st, RunParams p, WorkArrays wa,
-                                                         SpawnBuf sp, ClusterBuf cl, int enum_base)
+__device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, DevStep *st, const RunParams &p, const WorkArrays &wa,
+                                                         const SpawnBuf &sp, const ClusterBuf &cl, int enum_base)
 {
     __shared__ double smag[8];
     __shared__ u64 smf[64];
@@ -542,6 +542,7 @@ __global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(SysDev s, ListView L
     i64 inline_att = 0;
     i64 death_hf = 0;   // reference-cluster deaths, summed per block at the end
     // block-uniform loop: appends are reserved with one atomic per block
+    // (per-warp atomics on one counter contend at 1e8 samples per step)
     for (i64 g0 = (i64)blockIdx.x * blockDim.x; g0 < n_sel; g0 += (i64)gridDim.x * blockDim.x) {
         const i64 g = g0 + threadIdx.x;
         int nrec = 0;
@@ -678,8 +679,8 @@ __global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(SysDev s, ListView L
 // ---------------------------------------------------------------------------
 
 template <int K, typename R>
-__global__ void __launch_bounds__(WORK_THREADS, 4) k_attempts(SysDev s, ListView L, DevStep *st, RunParams p,
-                                                              WorkArrays wa, SpawnBuf sp, ClusterBuf cl)
+__device__ __forceinline__ void d_attempts(const SysDev &s, const ListView &L, DevStep *st, const RunParams &p,
+                                                              const WorkArrays &wa, const SpawnBuf &sp, const ClusterBuf &cl)
 {
     const i64 n = st->n_occ, tf = st->fnc_attempts;
     i64 ncl = (i64)(st->cl_packed >> CL_SHIFT);
@@ -742,7 +743,7 @@ __global__ void __launch_bounds__(WORK_THREADS, 4) k_attempts(SysDev s, ListView
 // a7: LSD radix sort by rank key (stable, fixed grid, digit-major offsets)
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(SORT_THREADS) k_sort_hist(const u64 *keys, const DevStep *st, i64 cap, int shift, int bits,
+__device__ __forceinline__ void d_sort_hist(const u64 *keys, const DevStep *st, i64 cap, int shift, int bits,
                                                              unsigned *hist)
 {
     __shared__ unsigned h[1 << MAX_DIGIT_BITS];
@@ -759,7 +760,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_hist(const u64 *keys, con
 
 // exclusive scan of row d (one digit across all sort blocks) in place, and
 // the row total; one block per digit
-__global__ void __launch_bounds__(1024) k_sort_scan(unsigned *hist, int grid, unsigned *totals)
+__device__ __forceinline__ void d_sort_scan(unsigned *hist, int grid, unsigned *totals)
 {
     __shared__ i64 sm[32];
     const int d = blockIdx.x;
@@ -775,7 +776,7 @@ __global__ void __launch_bounds__(1024) k_sort_scan(unsigned *hist, int grid, un
     if (threadIdx.x == 0) totals[d] = (unsigned)carry;
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const u64 *kin, const i64 *vin, u64 *kout, i64 *vout,
+__device__ __forceinline__ void d_sort_scatter(const u64 *kin, const i64 *vin, u64 *kout, i64 *vout,
                                                                 const DevStep *st, i64 cap, int shift, int bits,
                                                                 const unsigned *hist, const unsigned *totals)
 {
@@ -857,8 +858,8 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const u64 *kin, c
 // a8: one record per distinct key with the summed weight
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_seg_count(const u64 *keys, const DevStep *st, i64 cap, i64 *outpop,
-                                                             WorkArrays wa)
+__device__ __forceinline__ void d_seg_count(const u64 *keys, const DevStep *st, i64 cap, i64 *outpop,
+                                                             const WorkArrays &wa)
 {
     __shared__ i64 sm[32];
     i64 n = st->n_sp < cap ? st->n_sp : cap, lo, hi;
@@ -873,7 +874,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_seg_count(const u64 *keys, con
 }
 
 // generic: exclusive scan of part[4b + src] into part[4b + dst], total to *out
-__global__ void __launch_bounds__(1024) k_part_scan(WorkArrays wa, int grid, int src, int dst, i64 *out)
+__device__ __forceinline__ void d_part_scan(const WorkArrays &wa, int grid, int src, int dst, i64 *out)
 {
     __shared__ i64 sm[32];
     int t = threadIdx.x;
@@ -883,8 +884,8 @@ __global__ void __launch_bounds__(1024) k_part_scan(WorkArrays wa, int grid, int
     if (t == 0) *out = tot;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_seg_write(const u64 *keys, const i64 *pops, const DevStep *st, i64 cap,
-                                                             u64 *outkey, i64 *outpop, WorkArrays wa)
+__device__ __forceinline__ void d_seg_write(const u64 *keys, const i64 *pops, const DevStep *st, i64 cap,
+                                                             u64 *outkey, i64 *outpop, const WorkArrays &wa)
 {
     __shared__ i64 sm[32];
     i64 n = st->n_sp < cap ? st->n_sp : cap, lo, hi;
@@ -920,7 +921,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_seg_write(const u64 *keys, con
 // ---------------------------------------------------------------------------
 
 // each reduced key: add to its list entry, or mark it new (thresholded)
-__global__ void __launch_bounds__(WORK_THREADS) k_merge_match(ListView L, DevStep *st, RunParams p, WorkArrays wa,
+__device__ __forceinline__ void d_merge_match(const ListView &L, DevStep *st, const RunParams &p, const WorkArrays &wa,
                                                                const u64 *rkey, i64 *rpop)
 {
     const i64 n = st->n_occ, m = st->n_keys;
@@ -941,7 +942,7 @@ __global__ void __launch_bounds__(WORK_THREADS) k_merge_match(ListView L, DevSte
     }
 }
 
-__global__ void __launch_bounds__(WORK_THREADS) k_merge_list(ListView L, DevStep *st, RunParams p, WorkArrays wa)
+__device__ __forceinline__ void d_merge_list(const ListView &L, DevStep *st, const RunParams &p, const WorkArrays &wa)
 {
     const i64 n = st->n_occ;
     const u64 it = st->iter;
@@ -954,7 +955,7 @@ __global__ void __launch_bounds__(WORK_THREADS) k_merge_list(ListView L, DevStep
 }
 
 // counts of kept list entries (blocks [0, G)) and kept new keys ([G, 2G))
-__global__ void __launch_bounds__(SCAN_THREADS) k_keep_count(const DevStep *st, WorkArrays wa, int G)
+__device__ __forceinline__ void d_keep_count(const DevStep *st, const WorkArrays &wa, int G)
 {
     __shared__ i64 sm[32];
     const bool second = blockIdx.x >= G;
@@ -970,7 +971,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_keep_count(const DevStep *st, 
 }
 
 // exclusive prefixes of the keep flags in place
-__global__ void __launch_bounds__(SCAN_THREADS) k_keep_final(const DevStep *st, WorkArrays wa, int G)
+__device__ __forceinline__ void d_keep_final(const DevStep *st, const WorkArrays &wa, int G)
 {
     __shared__ i64 sm[32];
     const bool second = blockIdx.x >= G;
@@ -990,7 +991,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_keep_final(const DevStep *st, 
 }
 
 // scan of the 2G partials: list part then spawn part
-__global__ void __launch_bounds__(1024) k_keep_top(DevStep *st, WorkArrays wa, int G)
+__device__ __forceinline__ void d_keep_top(DevStep *st, const WorkArrays &wa, int G)
 {
     __shared__ i64 sm[32];
     int t = threadIdx.x;
@@ -1007,7 +1008,7 @@ __global__ void __launch_bounds__(1024) k_keep_top(DevStep *st, WorkArrays wa, i
 }
 
 template <int K>
-__global__ void __launch_bounds__(WORK_THREADS) k_scatter_list(SysDev s, ListView L, ListView O, DevStep *st, WorkArrays wa,
+__device__ __forceinline__ void d_scatter_list(const SysDev &s, const ListView &L, const ListView &O, DevStep *st, const WorkArrays &wa,
                                                                 const u64 *rkey)
 {
     __shared__ i64 sm[32];
@@ -1037,7 +1038,7 @@ __global__ void __launch_bounds__(WORK_THREADS) k_scatter_list(SysDev s, ListVie
 }
 
 template <int K, typename R>
-__global__ void __launch_bounds__(WORK_THREADS) k_scatter_new(SysDev s, ListView O, DevStep *st, WorkArrays wa,
+__device__ __forceinline__ void d_scatter_new(const SysDev &s, const ListView &O, DevStep *st, const WorkArrays &wa,
                                                                const u64 *rkey, const i64 *rpop)
 {
     __shared__ i64 sm[32];
@@ -1072,7 +1073,7 @@ __global__ void __launch_bounds__(WORK_THREADS) k_scatter_new(SysDev s, ListView
 // a10: estimator reduction and the per-step record
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(1024) k_finalize(DevStep *st, RunParams p, WorkArrays wa, ClusterBuf cl, int slots,
+__device__ __forceinline__ void d_finalize(DevStep *st, const RunParams &p, const WorkArrays &wa, const ClusterBuf &cl, int slots,
                                                    i64 list_cap)
 {
     __shared__ u64 smf[64];
@@ -1102,12 +1103,196 @@ __global__ void __launch_bounds__(1024) k_finalize(DevStep *st, RunParams p, Wor
         wa.ring[st->iter % RING] = r;
         st->n_start = st->n_occ;
         st->n_occ = r.nocc_after < list_cap ? r.nocc_after : list_cap;
+        st->cur ^= 1;   // the merged list becomes the current one
         st->iter = st->iter + 1;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Launcher
+// ---------------------------------------------------------------------------
+
+
+// ---------------------------------------------------------------------------
+// Kernels: each block serves replica blockIdx.y of an array of per-replica
+// arguments (one entry for a single context, many for a batch).
+// ---------------------------------------------------------------------------
+
+#define REPLICA                               \
+    const StepArgs &a = A[blockIdx.y];        \
+    const int cur_ = a.st->cur
+
+// the replica's arguments copied to shared memory (hot kernels)
+#define REPLICA_SMEM                                                              \
+    __shared__ StepArgs a_sm;                                                     \
+    {                                                                             \
+        const u64 *src_ = (const u64 *)&A[blockIdx.y];                            \
+        u64 *dst_ = (u64 *)&a_sm;                                                 \
+        for (int q_ = threadIdx.x; q_ < (int)(sizeof(StepArgs) / 8); q_ += blockDim.x) dst_[q_] = src_[q_]; \
+    }                                                                             \
+    __syncthreads();                                                              \
+    const StepArgs &a = a_sm;                                                     \
+    const int cur_ = a.st->cur
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_partial(const StepArgs *__restrict__ A)
+{
+    REPLICA;
+    d_scan_partial(a.list[cur_], a.st, a.p, a.wa);
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(const StepArgs *__restrict__ A, int grid)
+{
+    REPLICA;
+    d_scan_top(a.list[cur_], a.st, a.p, a.wa, grid, a.s.lmax);
+}
+
+template <int K, typename R>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(const StepArgs *__restrict__ A)
+{
+    REPLICA_SMEM;
+    d_scan_final<K, R>(a.s, a.list[cur_], a.st, a.p, a.wa);
+}
+
+template <int K, typename R>
+__global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(const StepArgs *__restrict__ A, int enum_base)
+{
+    REPLICA_SMEM;
+    d_sample<K, R>(a.s, a.list[cur_], a.st, a.p, a.wa, a.sp, a.cl, enum_base);
+}
+
+template <int K, typename R>
+__global__ void __launch_bounds__(WORK_THREADS, 4) k_attempts(const StepArgs *__restrict__ A)
+{
+    REPLICA_SMEM;
+    d_attempts<K, R>(a.s, a.list[cur_], a.st, a.p, a.wa, a.sp, a.cl);
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_hist(const StepArgs *__restrict__ A, int src, int shift, int bits)
+{
+    const StepArgs &a = A[blockIdx.y];
+    d_sort_hist(a.sp.key[src], a.st, a.sp.cap, shift, bits, a.wa.hist);
+}
+
+__global__ void __launch_bounds__(1024) k_sort_scan(const StepArgs *__restrict__ A, int grid)
+{
+    const StepArgs &a = A[blockIdx.y];
+    d_sort_scan(a.wa.hist, grid, a.wa.hist_tot);
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const StepArgs *__restrict__ A, int src, int shift, int bits)
+{
+    const StepArgs &a = A[blockIdx.y];
+    d_sort_scatter(a.sp.key[src], a.sp.pop[src], a.sp.key[src ^ 1], a.sp.pop[src ^ 1], a.st, a.sp.cap, shift, bits,
+                   a.wa.hist, a.wa.hist_tot);
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_seg_count(const StepArgs *__restrict__ A, int src)
+{
+    const StepArgs &a = A[blockIdx.y];
+    d_seg_count(a.sp.key[src], a.st, a.sp.cap, a.sp.pop[src ^ 1], a.wa);
+}
+
+__global__ void __launch_bounds__(1024) k_part_scan(const StepArgs *__restrict__ A, int grid)
+{
+    const StepArgs &a = A[blockIdx.y];
+    d_part_scan(a.wa, grid, 0, 2, &a.st->n_keys);
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_seg_write(const StepArgs *__restrict__ A, int src)
+{
+    const StepArgs &a = A[blockIdx.y];
+    d_seg_write(a.sp.key[src], a.sp.pop[src], a.st, a.sp.cap, a.sp.key[src ^ 1], a.sp.pop[src ^ 1], a.wa);
+}
+
+__global__ void __launch_bounds__(WORK_THREADS) k_merge_match(const StepArgs *__restrict__ A, int src)
+{
+    REPLICA;
+    d_merge_match(a.list[cur_], a.st, a.p, a.wa, a.sp.key[src ^ 1], a.sp.pop[src ^ 1]);
+}
+
+__global__ void __launch_bounds__(WORK_THREADS) k_merge_list(const StepArgs *__restrict__ A)
+{
+    REPLICA;
+    d_merge_list(a.list[cur_], a.st, a.p, a.wa);
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_keep_count(const StepArgs *__restrict__ A, int G)
+{
+    const StepArgs &a = A[blockIdx.y];
+    d_keep_count(a.st, a.wa, G);
+}
+
+__global__ void __launch_bounds__(1024) k_keep_top(const StepArgs *__restrict__ A, int G)
+{
+    const StepArgs &a = A[blockIdx.y];
+    d_keep_top(a.st, a.wa, G);
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_keep_final(const StepArgs *__restrict__ A, int G)
+{
+    const StepArgs &a = A[blockIdx.y];
+    d_keep_final(a.st, a.wa, G);
+}
+
+template <int K>
+__global__ void __launch_bounds__(WORK_THREADS) k_scatter_list(const StepArgs *__restrict__ A, int src)
+{
+    REPLICA;
+    d_scatter_list<K>(a.s, a.list[cur_], a.list[cur_ ^ 1], a.st, a.wa, a.sp.key[src ^ 1]);
+}
+
+template <int K, typename R>
+__global__ void __launch_bounds__(WORK_THREADS) k_scatter_new(const StepArgs *__restrict__ A, int src)
+{
+    REPLICA;
+    d_scatter_new<K, R>(a.s, a.list[cur_ ^ 1], a.st, a.wa, a.sp.key[src ^ 1], a.sp.pop[src ^ 1]);
+}
+
+__global__ void __launch_bounds__(1024) k_finalize(const StepArgs *__restrict__ A, int slots)
+{
+    REPLICA;
+    d_finalize(a.st, a.p, a.wa, a.cl, slots, a.list[cur_ ^ 1].cap);
+}
+
+// pointer-argument forms of the sort and reduction kernels (used without a context)
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_hist_p(const u64 *keys, const DevStep *st, i64 cap, int shift,
+                                                               int bits, unsigned *hist)
+{
+    d_sort_hist(keys, st, cap, shift, bits, hist);
+}
+
+__global__ void __launch_bounds__(1024) k_sort_scan_p(unsigned *hist, int grid, unsigned *totals)
+{
+    d_sort_scan(hist, grid, totals);
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter_p(const u64 *kin, const i64 *vin, u64 *kout, i64 *vout,
+                                                                  const DevStep *st, i64 cap, int shift, int bits,
+                                                                  const unsigned *hist, const unsigned *totals)
+{
+    d_sort_scatter(kin, vin, kout, vout, st, cap, shift, bits, hist, totals);
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_seg_count_p(const u64 *keys, const DevStep *st, i64 cap, i64 *outpop,
+                                                               WorkArrays wa)
+{
+    d_seg_count(keys, st, cap, outpop, wa);
+}
+
+__global__ void __launch_bounds__(1024) k_part_scan_p(WorkArrays wa, int grid, int src, int dst, i64 *out)
+{
+    d_part_scan(wa, grid, src, dst, out);
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_seg_write_p(const u64 *keys, const i64 *pops, const DevStep *st,
+                                                               i64 cap, u64 *outkey, i64 *outpop, WorkArrays wa)
+{
+    d_seg_write(keys, pops, st, cap, outkey, outpop, wa);
+}
+
+// ---------------------------------------------------------------------------
+// Launcher: the whole step for nrep replicas (grid dimension y), the same
+// sequence every step, so it can be captured once in a CUDA graph.
 // ---------------------------------------------------------------------------
 
 int bits_for(u64 bound)
@@ -1117,96 +1302,89 @@ int bits_for(u64 bound)
     return b;
 }
 
-template <int K, typename R>
-static cudaError_t launch_step_k(StepCtx &c)
+int sort_passes(const Shapes &sh)
 {
-    cudaStream_t sm = c.stream;
-    const Shapes &sh = c.sh;
-    ListView &L = c.list[c.cur];
-    ListView &O = c.list[c.cur ^ 1];
-    WorkArrays &wa = c.wa;
-    auto mark = [&](int phase) {
-        if (c.profile) cudaEventRecord(c.events[phase], sm);
-    };
+    return (sh.key_bits + sh.digit_bits - 1) / sh.digit_bits;
+}
 
-    // a1
+template <int K, typename R>
+static cudaError_t launch_phases(const StepArgs *A, int nrep, const Shapes &sh, bool multi_att, cudaStream_t sm,
+                                 i64 *launches, const cudaEvent_t *ev)
+{
+    auto mark = [&](int phase) {
+        if (ev) cudaEventRecord(ev[phase], sm);
+    };
+    const dim3 gscan(sh.scan_grid, nrep), gwork(sh.work_grid, nrep), gsort(sh.sort_grid, nrep), gone(1, nrep);
     mark(0);
-    k_scan_partial<<<sh.scan_grid, SCAN_THREADS, 0, sm>>>(L, c.st, c.prm, wa);
-    k_scan_top<<<1, 1024, 0, sm>>>(L, c.st, c.prm, wa, sh.scan_grid, c.sys.lmax);
-    k_scan_final<K, R><<<sh.scan_grid, SCAN_THREADS, 0, sm>>>(c.sys, L, c.st, c.prm, wa);
-    c.launches[0] += 3;
-    // a2-a5
+    k_scan_partial<<<gscan, SCAN_THREADS, 0, sm>>>(A);
+    k_scan_top<<<gone, 1024, 0, sm>>>(A, sh.scan_grid);
+    k_scan_final<K, R><<<gscan, SCAN_THREADS, 0, sm>>>(A);
+    launches[0] += 3;
     mark(1);
-    k_sample<K, R><<<sh.work_grid, WORK_THREADS, 0, sm>>>(c.sys, L, c.st, c.prm, wa, c.sp, c.cl, sh.scan_grid);
-    c.launches[1] += 1;
-    // a4/a6
+    k_sample<K, R><<<gwork, WORK_THREADS, 0, sm>>>(A, sh.scan_grid);
+    launches[1] += 1;
     mark(2);
-    if (c.prm.fnc || c.prm.multispawn) {
-        k_attempts<K, R><<<sh.work_grid, WORK_THREADS, 0, sm>>>(c.sys, L, c.st, c.prm, wa, c.sp, c.cl);
-        c.launches[2] += 1;
+    if (multi_att) {
+        k_attempts<K, R><<<gwork, WORK_THREADS, 0, sm>>>(A);
+        launches[2] += 1;
     }
-    // a7: radix sort of the spawned records
     mark(3);
     int src = 0;
     for (int shift = 0; shift < sh.key_bits; shift += sh.digit_bits) {
         int bits = min(sh.digit_bits, sh.key_bits - shift);
-        k_sort_hist<<<sh.sort_grid, SORT_THREADS, 0, sm>>>(c.sp.key[src], c.st, c.sp.cap, shift, bits, wa.hist);
-        k_sort_scan<<<1 << bits, 1024, 0, sm>>>(wa.hist, sh.sort_grid, wa.hist_tot);
-        k_sort_scatter<<<sh.sort_grid, SORT_THREADS, 0, sm>>>(c.sp.key[src], c.sp.pop[src], c.sp.key[src ^ 1],
-                                                               c.sp.pop[src ^ 1], c.st, c.sp.cap, shift, bits, wa.hist,
-                                                               wa.hist_tot);
+        k_sort_hist<<<gsort, SORT_THREADS, 0, sm>>>(A, src, shift, bits);
+        k_sort_scan<<<dim3(1 << bits, nrep), 1024, 0, sm>>>(A, sh.sort_grid);
+        k_sort_scatter<<<gsort, SORT_THREADS, 0, sm>>>(A, src, shift, bits);
         src ^= 1;
-        c.launches[3] += 3;
+        launches[3] += 3;
     }
-    c.sorted_buf = src;
-    const u64 *skey = c.sp.key[src];
-    const i64 *spop = c.sp.pop[src];
-    u64 *rkey = c.sp.key[src ^ 1];
-    i64 *rpop = c.sp.pop[src ^ 1];
-
-    // a8: reduction of equal keys
     mark(4);
-    k_seg_count<<<sh.scan_grid, SCAN_THREADS, 0, sm>>>(skey, c.st, c.sp.cap, rpop, wa);
-    k_part_scan<<<1, 1024, 0, sm>>>(wa, sh.scan_grid, 0, 2, &c.st->n_keys);
-    k_seg_write<<<sh.scan_grid, SCAN_THREADS, 0, sm>>>(skey, spop, c.st, c.sp.cap, rkey, rpop, wa);
-    c.launches[4] += 3;
-
-    // a9: merge
+    k_seg_count<<<gscan, SCAN_THREADS, 0, sm>>>(A, src);
+    k_part_scan<<<gone, 1024, 0, sm>>>(A, sh.scan_grid);
+    k_seg_write<<<gscan, SCAN_THREADS, 0, sm>>>(A, src);
+    launches[4] += 3;
     mark(5);
-    k_merge_match<<<sh.work_grid, WORK_THREADS, 0, sm>>>(L, c.st, c.prm, wa, rkey, rpop);
-    k_merge_list<<<sh.work_grid, WORK_THREADS, 0, sm>>>(L, c.st, c.prm, wa);
-    k_keep_count<<<2 * sh.scan_grid, SCAN_THREADS, 0, sm>>>(c.st, wa, sh.scan_grid);
-    k_keep_top<<<1, 1024, 0, sm>>>(c.st, wa, sh.scan_grid);
-    k_keep_final<<<2 * sh.scan_grid, SCAN_THREADS, 0, sm>>>(c.st, wa, sh.scan_grid);
-    k_scatter_list<K><<<sh.work_grid, WORK_THREADS, 0, sm>>>(c.sys, L, O, c.st, wa, rkey);
-    k_scatter_new<K, R><<<sh.work_grid, WORK_THREADS, 0, sm>>>(c.sys, O, c.st, wa, rkey, rpop);
-    c.launches[5] += 7;
-
-    // a10
+    k_merge_match<<<gwork, WORK_THREADS, 0, sm>>>(A, src);
+    k_merge_list<<<gwork, WORK_THREADS, 0, sm>>>(A);
+    k_keep_count<<<dim3(2 * sh.scan_grid, nrep), SCAN_THREADS, 0, sm>>>(A, sh.scan_grid);
+    k_keep_top<<<gone, 1024, 0, sm>>>(A, sh.scan_grid);
+    k_keep_final<<<dim3(2 * sh.scan_grid, nrep), SCAN_THREADS, 0, sm>>>(A, sh.scan_grid);
+    k_scatter_list<K><<<gwork, WORK_THREADS, 0, sm>>>(A, src);
+    k_scatter_new<K, R><<<gwork, WORK_THREADS, 0, sm>>>(A, src);
+    launches[5] += 7;
     mark(6);
-    k_finalize<<<1, 1024, 0, sm>>>(c.st, c.prm, wa, c.cl, sh.enum_slots, O.cap);
-    c.launches[6] += 1;
+    k_finalize<<<gone, 1024, 0, sm>>>(A, sh.enum_slots);
+    launches[6] += 1;
     mark(7);
-    c.cur ^= 1;
     return cudaGetLastError();
+}
+
+cudaError_t launch_group(const StepArgs *A, int nrep, int K, bool fp32, const Shapes &sh, bool multi_att,
+                         cudaStream_t sm, i64 *launches, const cudaEvent_t *ev)
+{
+    if (fp32) {
+        switch (K) {
+        case 1: return launch_phases<1, float>(A, nrep, sh, multi_att, sm, launches, ev);
+        case 2: return launch_phases<2, float>(A, nrep, sh, multi_att, sm, launches, ev);
+        case 3: return launch_phases<3, float>(A, nrep, sh, multi_att, sm, launches, ev);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (K) {
+    case 1: return launch_phases<1, double>(A, nrep, sh, multi_att, sm, launches, ev);
+    case 2: return launch_phases<2, double>(A, nrep, sh, multi_att, sm, launches, ev);
+    case 3: return launch_phases<3, double>(A, nrep, sh, multi_att, sm, launches, ev);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_step(StepCtx &c)
 {
-    if (c.fp32) {
-        switch (c.K) {
-        case 1: return launch_step_k<1, float>(c);
-        case 2: return launch_step_k<2, float>(c);
-        case 3: return launch_step_k<3, float>(c);
-        default: return cudaErrorInvalidValue;
-        }
-    }
-    switch (c.K) {
-    case 1: return launch_step_k<1, double>(c);
-    case 2: return launch_step_k<2, double>(c);
-    case 3: return launch_step_k<3, double>(c);
-    default: return cudaErrorInvalidValue;
-    }
+    cudaError_t e = launch_group(c.d_args, 1, c.K, c.fp32, c.sh, c.prm.fnc || c.prm.multispawn, c.stream, c.launches,
+                                 c.profile ? c.events : nullptr);
+    c.sorted_buf = sort_passes(c.sh) & 1;
+    c.cur ^= 1;
+    return e;
 }
 
 }  // namespace ccmc
@@ -1294,9 +1472,9 @@ extern "C" ccmc_status ccmc_reduce_records_noalloc(const uint64_t *keys_in, cons
     int dst = 0;
     for (int shift = 0; shift < key_bits; shift += MAX_DIGIT_BITS) {
         int bits = key_bits - shift < MAX_DIGIT_BITS ? key_bits - shift : MAX_DIGIT_BITS;
-        k_sort_hist<<<NOALLOC_GRID, SORT_THREADS, 0, sm>>>(kin, &S->st, cap, shift, bits, S->hist);
-        k_sort_scan<<<1 << bits, 1024, 0, sm>>>(S->hist, NOALLOC_GRID, S->tot);
-        k_sort_scatter<<<NOALLOC_GRID, SORT_THREADS, 0, sm>>>(kin, vin, S->key[dst], S->pop[dst], &S->st, cap, shift,
+        k_sort_hist_p<<<NOALLOC_GRID, SORT_THREADS, 0, sm>>>(kin, &S->st, cap, shift, bits, S->hist);
+        k_sort_scan_p<<<1 << bits, 1024, 0, sm>>>(S->hist, NOALLOC_GRID, S->tot);
+        k_sort_scatter_p<<<NOALLOC_GRID, SORT_THREADS, 0, sm>>>(kin, vin, S->key[dst], S->pop[dst], &S->st, cap, shift,
                                                                bits, S->hist, S->tot);
         kin = S->key[dst];
         vin = S->pop[dst];
@@ -1306,9 +1484,9 @@ extern "C" ccmc_status ccmc_reduce_records_noalloc(const uint64_t *keys_in, cons
     WorkArrays wa;
     memset(&wa, 0, sizeof(wa));
     wa.part = S->part;
-    k_seg_count<<<NOALLOC_GRID, SCAN_THREADS, 0, sm>>>(kin, &S->st, cap, (i64 *)pops_out, wa);
-    k_part_scan<<<1, 1024, 0, sm>>>(wa, NOALLOC_GRID, 0, 2, &S->st.n_keys);
-    k_seg_write<<<NOALLOC_GRID, SCAN_THREADS, 0, sm>>>(kin, vin, &S->st, cap, (u64 *)keys_out, (i64 *)pops_out, wa);
+    k_seg_count_p<<<NOALLOC_GRID, SCAN_THREADS, 0, sm>>>(kin, &S->st, cap, (i64 *)pops_out, wa);
+    k_part_scan_p<<<1, 1024, 0, sm>>>(wa, NOALLOC_GRID, 0, 2, &S->st.n_keys);
+    k_seg_write_p<<<NOALLOC_GRID, SCAN_THREADS, 0, sm>>>(kin, vin, &S->st, cap, (u64 *)keys_out, (i64 *)pops_out, wa);
     if (cudaGetLastError() != cudaSuccess) return CCMC_ERR_CUDA;
     i64 m = 0;
     if (cudaMemcpyAsync(&m, &S->st.n_keys, sizeof(i64), cudaMemcpyDeviceToHost, sm) != cudaSuccess) return CCMC_ERR_CUDA;

@@ -223,6 +223,26 @@ def test_fp32_estimator_accuracy_on_one_state(ccmc):
     assert 0.0 < rel < 1e-5
 
 
+def test_graph_replay_equals_kernel_launches(ccmc):
+    """On a stream the step is replayed from a captured CUDA graph; it must
+    give the same trajectory as launching the kernels one by one."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA")
+    w = workload("ueg14_m114_ccsdt_fnc_ms")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    g = ccmc.from_workload(w, stream=s1.cuda_stream)
+    e = ccmc.from_workload(w, stream=s2.cuda_stream, use_graph=False)
+    for _ in range(8):
+        g.step(25)
+        e.step(25)
+        assert g.records() == e.records()
+    for x, y in zip(g.get_list(), e.get_list()):
+        assert np.array_equal(x, y)
+    _, _, total = g.phase_times()
+    assert total > 0
+
+
 def test_negative_reference_weight(ccmc):
     """A wavefunction with a negative reference weight evolves identically."""
     w = workload("ueg14_m38_ccsd")
