@@ -403,6 +403,160 @@ def read_traffic(workload: str, phase: str):
     return None
 
 
+def run_gpu_batched(args):
+    """64 independent UEG problems (14 electrons, M in {38,54,66,114} x r_s in
+    {0.5,1,2,5}, CCSD/CCSDT, targets 1e4-1e6) stepped as one batch: one launch
+    per phase over all replicas of a word count, replayed from a CUDA graph.
+    The same states are then stepped one context after another for
+    comparison; the two must give bit-identical lists."""
+    import numpy as np
+    import torch
+
+    import paper_1807_03749_gb300 as ccmc
+    from ccmc_inputs import batched_replicas
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    reps = batched_replicas(64)
+    stream = torch.cuda.Stream()
+    ctxs = [ccmc.from_workload(w, stream=stream.cuda_stream) for w in reps]
+    batch = ccmc.Batch(ctxs, stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    t_grow = time.perf_counter()
+    grown, reached = 0, None
+    while grown < args.grow_max:
+        batch.step(10)
+        grown += 10
+        states = [c.get_state() for c in ctxs]
+        if time.perf_counter() - t_grow > args.grow_seconds:
+            raise RuntimeError(f"batched growth did not settle within {args.grow_seconds} s ({grown} steps)")
+        if grown % 100 == 0:
+            for c in ctxs:
+                en = c.energy()
+                if en["n_total"] > 1e3 * max(en["n0"], 1.0):
+                    raise RuntimeError(f"growth did not settle: N_total={en['n_total']:.3e}, t_HF={en['n0']:.3e}")
+        if reached is None and all(st[2] for st in states):
+            reached = grown
+        if reached is not None and grown >= reached + args.equilibrate:
+            break
+    t_grow = time.perf_counter() - t_grow
+    for c in ctxs:
+        c.records()
+
+    def timed(step_fn, strm, nsteps):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
+        with torch.cuda.stream(strm):
+            for k in range(nsteps):
+                flush.fill_(k)
+                starts[k].record(strm)
+                step_fn()
+                ends[k].record(strm)
+        strm.synchronize()
+        return sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+
+    timed(lambda: batch.step(1), stream, args.warmup)
+    for c in ctxs:
+        c.records()
+    with tempfile.TemporaryDirectory() as tmp:
+        paths = [os.path.join(tmp, f"r{i}.ck") for i in range(len(ctxs))]
+        for c, pth in zip(ctxs, paths):
+            c.save(pth)
+        _, _, launches0 = batch.phase_times()
+        clocks = ClockSampler(local)
+        clocks.start()
+        torch.cuda.synchronize()
+        ms_batched = timed(lambda: batch.step(1), stream, args.steps)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        _, _, launches1 = batch.phase_times()
+        recs = [c.records() for c in ctxs]
+        samples = sum(r["n_sel"] + r["n_visit"] for rr in recs for r in rr)
+        keys = sum(r["n_spawned"] for rr in recs for r in rr)
+        final = [c.get_list() for c in ctxs]
+
+        # the same steps from the same states, one context after another
+        seq_stream = torch.cuda.Stream()
+        seq = [ccmc.from_workload(w, stream=seq_stream.cuda_stream) for w in reps]
+        for c, pth in zip(seq, paths):
+            c.load(pth)
+
+        def seq_step():
+            for c in seq:
+                c.step(1)
+
+        seq_step()  # graph capture of every context, then back to the saved states
+        for c, pth in zip(seq, paths):
+            c.load(pth)
+        torch.cuda.synchronize()
+        ms_seq = timed(seq_step, seq_stream, args.steps)
+        identical = all(all(np.array_equal(x, y) for x, y in zip(f, c.get_list())) for f, c in zip(final, seq))
+        for c in seq:
+            c.close()
+        del seq
+
+    # per-phase timers (events between phases of every word-count group)
+    batch.profile(True)
+    timed(lambda: batch.step(1), stream, args.profile_steps)
+    pms, _, _ = batch.phase_times()
+    batch.profile(False)
+    nprof = max(1, args.profile_steps)
+    precs = [c.records()[-nprof:] for c in ctxs]
+    dom = max(pms, key=lambda q: pms[q])
+    dom_ms = pms[dom] / nprof
+    alg = sum(algorithmic_bytes(dom, rr, c.nw) for rr, c in zip(precs, ctxs))
+    hbm, src = peaks()
+    achieved = alg / (dom_ms * 1e-3) / 1e9
+
+    # end to end: every replica's list from host memory, one batched step,
+    # every list and estimator back to the host
+    lists = [c.get_list() for c in ctxs]
+    h2d = d2h = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.e2e_steps):
+        for c, (bits, _, pop) in zip(ctxs, lists):
+            c.set_list(bits, pop)
+            h2d += bits.nbytes + pop.nbytes
+        batch.step(1)
+        lists = [c.get_list() for c in ctxs]
+        for c, (bits, kk, pop) in zip(ctxs, lists):
+            c.energy()
+            d2h += bits.nbytes + kk.nbytes + pop.nbytes + 40
+    torch.cuda.synchronize()
+    e2e_secs = time.perf_counter() - t0
+    e2e_samples = sum(r["n_sel"] + r["n_visit"] for c in ctxs for r in c.records()[-args.e2e_steps:])
+    info = batch.info()
+    cpu = None if args.no_cpu_baseline else cpu_baseline(reps[-1])
+    value = samples / (ms_batched * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_batched / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "keys_per_s": keys / (ms_batched * 1e-3),
+        "config": {"workload": "batched64_ueg14", "replicas": len(ctxs),
+                   "systems": "14 e, M in {38,54,66,114} x r_s in {0.5,1,2,5}, CCSD (r<16, 32<=r<48) else CCSDT, "
+                              "target 10^(4 + r mod 3), dtau 0.01, original sampler",
+                   "state": f"grown from HF for {grown} steps ({t_grow:.1f} s), every shift varying",
+                   "n_total": sum(rr[-1]["ntot_after"] for rr in recs) / 65536.0,
+                   "sequential_samples_per_s": samples / (ms_seq * 1e-3),
+                   "batched_speedup_over_sequential": ms_seq / ms_batched,
+                   "bit_identical_to_sequential": identical, "tuned_shapes": info,
+                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas64"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                     "phase_ms_per_step": {k: v / nprof for k, v in pms.items()},
+                     "algorithmic_bytes_per_launch": alg},
+        "clocks": clk,
+        "e2e": {"value": e2e_samples / e2e_secs, "unit": "samples/s",
+                "h2d_bytes_per_step": h2d // max(1, args.e2e_steps),
+                "d2h_bytes_per_step": d2h // max(1, args.e2e_steps)},
+        "gpu_launches": int(launches1 - launches0),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(w):
     """The oracle on one host core, on slices of one full step at the target
     size (about 10 s of CPU work)."""
@@ -441,6 +595,15 @@ def main():
     over = {}
     if args.target_pop:
         over["target_pop"] = args.target_pop   # smaller cases of a workload for profiling
+    if args.workload == "batched64_ueg14":
+        if args.impl == "reference":
+            from ccmc_inputs import batched_replicas
+
+            # one replica (r = 63: M = 114, r_s = 5, CCSDT, target 1e4) as the oracle's sample
+            run_reference(args, dict(batched_replicas(64)[-1], name="batched64_ueg14"))
+        else:
+            run_gpu_batched(args)
+        return
     w = workload(args.workload, **over)
     if args.impl == "reference":
         run_reference(args, w)

@@ -223,6 +223,39 @@ ccmc_status ccmc_profile(ccmc_ctx *ctx, int32_t enable);
  * number of kernels launched by ccmc_step since the context was created. */
 ccmc_status ccmc_phase_times(ccmc_ctx *ctx, double *ms, int64_t *launches, int32_t nphases, int64_t *total_launches);
 
+/* ---- Batched form: many independent contexts stepped together ----------
+ * Every phase of the step is one kernel launch over all replicas that share
+ * a determinant word count and precision (a CUDA grid dimension indexes the
+ * replica), and the whole step is captured once in a CUDA graph and replayed.
+ * Per-replica grid sizes and the radix digit width are chosen by timing
+ * candidates on the first steps (the trajectory does not depend on them).
+ * Replicas keep their own Philox keys, shift control and checkpoints; results
+ * are bit-identical to stepping each context alone. */
+typedef struct ccmc_batch ccmc_batch;
+
+/* Groups n contexts (which must all use the same shift_a) into a batch whose
+ * work is issued on cuda_stream (must not be NULL).  The contexts stay owned
+ * by the caller and must not be stepped on their own while in the batch. */
+ccmc_status ccmc_batch_create(ccmc_ctx **ctxs, int32_t n, void *cuda_stream, ccmc_batch **out);
+
+/* nsteps steps of every context in the batch.  The host synchronises at each
+ * context's shift-update boundary (every shift_a steps).  The first call
+ * times tuning candidates on its first steps before capturing the graph. */
+ccmc_status ccmc_step_batched(ccmc_batch *b, int32_t nsteps);
+
+/* The tuned per-replica work-grid blocks and radix digit width (after the
+ * first ccmc_step_batched), and the number of replica groups. */
+ccmc_status ccmc_batch_info(ccmc_batch *b, int32_t *work_blocks, int32_t *digit_bits, int32_t *groups);
+
+/* Per-phase timers of the batch, as ccmc_profile / ccmc_phase_times for a
+ * context (phases summed over the replica groups). */
+ccmc_status ccmc_batch_profile(ccmc_batch *b, int32_t enable);
+ccmc_status ccmc_batch_phase_times(ccmc_batch *b, double *ms, int64_t *launches, int32_t nphases,
+                                   int64_t *total_launches);
+
+/* Releases the batch (not its contexts). */
+void ccmc_batch_free(ccmc_batch *b);
+
 /* Largest record count accepted by ccmc_reduce_records_noalloc. */
 #define CCMC_NOALLOC_MAX_RECORDS 65536
 

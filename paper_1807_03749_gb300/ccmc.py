@@ -66,7 +66,8 @@ EXPORTS = [
     "ccmc_init", "ccmc_step", "ccmc_energy", "ccmc_reference_energy", "ccmc_get_records", "ccmc_list_size",
     "ccmc_get_list", "ccmc_set_list", "ccmc_get_spawned", "ccmc_get_death", "ccmc_set_state", "ccmc_get_state",
     "ccmc_save", "ccmc_load", "ccmc_sync", "ccmc_last_error", "ccmc_free", "ccmc_profile", "ccmc_phase_times",
-    "ccmc_reduce_records_noalloc",
+    "ccmc_reduce_records_noalloc", "ccmc_batch_create", "ccmc_step_batched", "ccmc_batch_info", "ccmc_batch_free",
+    "ccmc_batch_profile", "ccmc_batch_phase_times",
 ]
 
 PHASES = ["scan", "sample", "attempts", "sort", "reduce", "merge", "finalize"]
@@ -102,6 +103,12 @@ def load(path: str | None = None):
         "ccmc_profile": (c_int, [vp, c_int32]),
         "ccmc_phase_times": (c_int, [vp, dp, i64p, c_int32, i64p]),
         "ccmc_reduce_records_noalloc": (c_int, [vp, vp, c_size_t, c_int32, vp, vp, POINTER(c_size_t), vp]),
+        "ccmc_batch_create": (c_int, [POINTER(c_void_p), c_int32, vp, POINTER(c_void_p)]),
+        "ccmc_step_batched": (c_int, [vp, c_int32]),
+        "ccmc_batch_info": (c_int, [vp, i32p, i32p, i32p]),
+        "ccmc_batch_free": (None, [vp]),
+        "ccmc_batch_profile": (c_int, [vp, c_int32]),
+        "ccmc_batch_phase_times": (c_int, [vp, dp, i64p, c_int32, i64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -293,6 +300,56 @@ class Context:
         self._check(self._lib.ccmc_phase_times(self._h, _ptr(ms, c_double), _ptr(la, c_int64), len(PHASES),
                                                ctypes.byref(tot)))
         return dict(zip(PHASES, ms.tolist())), dict(zip(PHASES, la.tolist())), int(tot.value)
+
+
+class Batch:
+    """Several contexts stepped together (one launch per phase over all of
+    them, replayed from a CUDA graph).  The contexts stay usable for reading
+    results and checkpoints but must not be stepped on their own."""
+
+    def __init__(self, contexts, stream):
+        L = load()
+        self._lib = L
+        self.contexts = list(contexts)
+        arr = (c_void_p * len(self.contexts))(*[c._h.value for c in self.contexts])
+        h = c_void_p(0)
+        st = L.ccmc_batch_create(arr, len(self.contexts), c_void_p(int(stream)), ctypes.byref(h))
+        if st != 0:
+            raise CCMCError(st, "ccmc_batch_create failed")
+        self._h = h
+
+    def step(self, nsteps: int = 1):
+        st = self._lib.ccmc_step_batched(self._h, nsteps)
+        if st != 0:
+            raise CCMCError(st, "ccmc_step_batched failed")
+
+    def info(self) -> dict:
+        w, d, g = c_int32(0), c_int32(0), c_int32(0)
+        self._lib.ccmc_batch_info(self._h, ctypes.byref(w), ctypes.byref(d), ctypes.byref(g))
+        return {"work_blocks": w.value, "digit_bits": d.value, "groups": g.value}
+
+    def profile(self, enable: bool = True):
+        if self._lib.ccmc_batch_profile(self._h, int(enable)):
+            raise CCMCError(2, "ccmc_batch_profile failed")
+
+    def phase_times(self):
+        ms = np.zeros(len(PHASES), dtype=np.float64)
+        la = np.zeros(len(PHASES), dtype=np.int64)
+        tot = c_int64(0)
+        self._lib.ccmc_batch_phase_times(self._h, _ptr(ms, c_double), _ptr(la, c_int64), len(PHASES),
+                                         ctypes.byref(tot))
+        return dict(zip(PHASES, ms.tolist())), dict(zip(PHASES, la.tolist())), int(tot.value)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.ccmc_batch_free(self._h)
+            self._h = c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def from_workload(w: dict, **overrides) -> Context:

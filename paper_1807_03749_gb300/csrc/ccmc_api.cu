@@ -965,3 +965,365 @@ void ccmc_free(ccmc_ctx *ctx)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched form
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// latest record and error word of every replica, for the host's shift control
+__global__ void k_batch_gather(const StepArgs *A, int n, Record *out, unsigned *err)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const DevStep *st = A[r].st;
+    out[r] = A[r].wa.ring[(st->iter + RING - 1) % RING];
+    err[r] = st->err;
+}
+
+__global__ void k_batch_shift(const StepArgs *A, int n, const double *shift)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) A[r].st->shift = shift[r];
+}
+
+struct BatchGroup {
+    int K = 1;
+    bool fp32 = false, multi = false;
+    std::vector<int> members;
+    StepArgs *d_args = nullptr;
+    int key_bits = 1;
+};
+
+}  // namespace
+
+struct ccmc_batch {
+    std::vector<ccmc_ctx *> ctxs;
+    cudaStream_t stream = nullptr;
+    std::vector<BatchGroup> groups;
+    StepArgs *d_all = nullptr;       // every replica, for gather / shift scatter
+    Record *d_rec = nullptr, *h_rec = nullptr;
+    unsigned *d_err = nullptr, *h_err = nullptr;
+    double *d_shift = nullptr, *h_shift = nullptr;
+    Shapes sh;                        // per-replica shapes (key_bits set per group)
+    bool tuned = false;
+    cudaGraphExec_t graph = nullptr;
+    i64 launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    i64 graph_launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    std::vector<void *> blocks;
+    // opt-in phase timers
+    bool profile = false;
+    std::vector<cudaEvent_t> events;   // 8 per group
+    double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    i64 launch0[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+cudaError_t batch_launch(ccmc_batch *b, const Shapes &base)
+{
+    for (size_t gi = 0; gi < b->groups.size(); gi++) {
+        BatchGroup &g = b->groups[gi];
+        Shapes sh = base;
+        sh.key_bits = g.key_bits;
+        const cudaEvent_t *ev = b->profile ? &b->events[8 * gi] : nullptr;
+        cudaError_t e = launch_group(g.d_args, (int)g.members.size(), g.K, g.fp32, sh, g.multi, b->stream,
+                                     b->launches, ev);
+        if (e != cudaSuccess) return e;
+    }
+    if (b->profile) {
+        for (size_t gi = 0; gi < b->groups.size(); gi++) {
+            if (cudaEventSynchronize(b->events[8 * gi + NPHASES]) != cudaSuccess) return cudaErrorUnknown;
+            for (int ph = 0; ph < NPHASES; ph++) {
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, b->events[8 * gi + ph], b->events[8 * gi + ph + 1]);
+                b->phase_ms[ph] += ms;
+            }
+        }
+    }
+    return cudaSuccess;
+}
+
+void batch_after_step(ccmc_batch *b)
+{
+    for (BatchGroup &g : b->groups) {
+        Shapes sh = b->sh;
+        sh.key_bits = g.key_bits;
+        for (int m : g.members) {
+            ccmc_ctx *c = b->ctxs[m];
+            c->sc.cur ^= 1;
+            c->sc.sorted_buf = sort_passes(sh) & 1;
+            c->stepped = true;
+            c->iter++;
+        }
+    }
+}
+
+// shift control for the contexts that reached a boundary with this step
+ccmc_status batch_boundaries(ccmc_batch *b)
+{
+    const int n = (int)b->ctxs.size();
+    bool any = false;
+    for (ccmc_ctx *c : b->ctxs) any = any || (c->iter % (u64)c->prm.shift_a) == 0;
+    if (!any) return CCMC_OK;
+    k_batch_gather<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_all, n, b->d_rec, b->d_err);
+    if (cudaMemcpyAsync(b->h_rec, b->d_rec, sizeof(Record) * n, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->h_err, b->d_err, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return CCMC_ERR_CUDA;
+    bool changed = false;
+    for (int r = 0; r < n; r++) {
+        ccmc_ctx *c = b->ctxs[r];
+        if (b->h_err[r]) return status_from_bits(c, b->h_err[r]);
+        b->h_shift[r] = c->shift;
+        if ((c->iter % (u64)c->prm.shift_a) != 0) continue;
+        const int A = c->prm.shift_a;
+        double nt = (double)b->h_rec[r].ntot_after / 65536.0;
+        double prev = c->shift;
+        if (c->vary && nt > 0.0 && c->nprev > 0.0)
+            c->shift = c->shift - (c->prm.zeta / ((double)A * c->prm.tau)) * std::log(nt / c->nprev);
+        if (!c->vary && nt > c->prm.target_pop) c->vary = 1;
+        c->nprev = nt;
+        b->h_shift[r] = c->shift;
+        changed = changed || c->shift != prev;
+    }
+    if (changed) {
+        if (cudaMemcpyAsync(b->d_shift, b->h_shift, sizeof(double) * n, cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess)
+            return CCMC_ERR_CUDA;
+        k_batch_shift<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_all, n, b->d_shift);
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess) return CCMC_ERR_CUDA;
+    }
+    return CCMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ccmc_status ccmc_batch_create(ccmc_ctx **ctxs, int32_t n, void *cuda_stream, ccmc_batch **out)
+{
+    if (!out) return CCMC_ERR_ARG;
+    *out = nullptr;
+    if (!ctxs || n < 1 || !cuda_stream) return CCMC_ERR_ARG;
+    for (int r = 0; r < n; r++) {
+        if (!ctxs[r] || ctxs[r]->prm.shift_a != ctxs[0]->prm.shift_a) return CCMC_ERR_ARG;
+        for (int q = 0; q < r; q++)
+            if (ctxs[q] == ctxs[r]) return CCMC_ERR_ARG;
+    }
+    ccmc_batch *b = new (std::nothrow) ccmc_batch();
+    if (!b) return CCMC_ERR_OOM;
+    b->ctxs.assign(ctxs, ctxs + n);
+    b->stream = (cudaStream_t)cuda_stream;
+    for (int r = 0; r < n; r++) {
+        ccmc_ctx *c = ctxs[r];
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            delete b;
+            return CCMC_ERR_CUDA;
+        }
+        bool multi = c->prm.fnc || c->prm.multispawn;
+        bool fp32 = c->sc.fp32;
+        BatchGroup *g = nullptr;
+        for (BatchGroup &x : b->groups)
+            if (x.K == c->sc.K && x.fp32 == fp32) g = &x;
+        if (!g) {
+            b->groups.emplace_back();
+            g = &b->groups.back();
+            g->K = c->sc.K;
+            g->fp32 = fp32;
+        }
+        g->multi = g->multi || multi;
+        g->members.push_back(r);
+        g->key_bits = std::max(g->key_bits, c->sc.sh.key_bits);
+    }
+    auto dalloc = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        b->blocks.push_back(p);
+        return p;
+    };
+    std::vector<StepArgs> all(n);
+    for (int r = 0; r < n; r++) all[r] = ctxs[r]->sc.h_args;
+    b->d_all = (StepArgs *)dalloc(sizeof(StepArgs) * n);
+    b->d_rec = (Record *)dalloc(sizeof(Record) * n);
+    b->d_err = (unsigned *)dalloc(sizeof(unsigned) * n);
+    b->d_shift = (double *)dalloc(sizeof(double) * n);
+    bool ok = b->d_all && b->d_rec && b->d_err && b->d_shift &&
+              cudaMallocHost(&b->h_rec, sizeof(Record) * n) == cudaSuccess &&
+              cudaMallocHost(&b->h_err, sizeof(unsigned) * n) == cudaSuccess &&
+              cudaMallocHost(&b->h_shift, sizeof(double) * n) == cudaSuccess &&
+              cudaMemcpy(b->d_all, all.data(), sizeof(StepArgs) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+    for (BatchGroup &g : b->groups) {
+        std::vector<StepArgs> ga;
+        for (int m : g.members) ga.push_back(all[m]);
+        g.d_args = (StepArgs *)dalloc(sizeof(StepArgs) * ga.size());
+        ok = ok && g.d_args &&
+             cudaMemcpy(g.d_args, ga.data(), sizeof(StepArgs) * ga.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    // per-replica shapes may not exceed what every context allocated for
+    Shapes lim = ctxs[0]->sc.sh;
+    for (int r = 1; r < n; r++) {
+        lim.scan_grid = std::min(lim.scan_grid, ctxs[r]->sc.sh.scan_grid);
+        lim.work_grid = std::min(lim.work_grid, ctxs[r]->sc.sh.work_grid);
+        lim.sort_grid = std::min(lim.sort_grid, ctxs[r]->sc.sh.sort_grid);
+    }
+    b->sh = lim;
+    b->sh.work_grid = std::min(lim.work_grid, 16);
+    b->sh.scan_grid = std::min(lim.scan_grid, 8);
+    b->sh.sort_grid = std::min(lim.sort_grid, 8);
+    b->sh.digit_bits = MAX_DIGIT_BITS;
+    b->sh.enum_slots = b->sh.scan_grid + b->sh.work_grid;
+    if (!ok) {
+        ccmc_batch_free(b);
+        return CCMC_ERR_OOM;
+    }
+    *out = b;
+    return CCMC_OK;
+}
+
+ccmc_status ccmc_step_batched(ccmc_batch *b, int32_t nsteps)
+{
+    if (!b || nsteps < 0) return CCMC_ERR_ARG;
+    int k = 0;
+    if (!b->tuned && nsteps > 0) {
+        // time candidate shapes on real steps (results do not depend on them)
+        const int wcand[] = {8, 16, 32, 64};
+        const int dcand[] = {6, 8};
+        Shapes best = b->sh;
+        float best_ms = 1e30f;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (int wi = 0; wi < 4 && k < nsteps; wi++)
+            for (int di = 0; di < 2 && k < nsteps; di++) {
+                Shapes sh = b->sh;
+                Shapes lim = b->ctxs[0]->sc.sh;
+                for (ccmc_ctx *c : b->ctxs) {
+                    lim.work_grid = std::min(lim.work_grid, c->sc.sh.work_grid);
+                    lim.scan_grid = std::min(lim.scan_grid, c->sc.sh.scan_grid);
+                    lim.sort_grid = std::min(lim.sort_grid, c->sc.sh.sort_grid);
+                }
+                sh.work_grid = std::min(wcand[wi], lim.work_grid);
+                sh.scan_grid = std::min(std::max(2, wcand[wi] / 2), lim.scan_grid);
+                sh.sort_grid = std::min(std::max(2, wcand[wi] / 2), lim.sort_grid);
+                sh.digit_bits = dcand[di];
+                sh.enum_slots = sh.scan_grid + sh.work_grid;
+                b->sh = sh;
+                cudaEventRecord(e0, b->stream);
+                cudaError_t e = batch_launch(b, sh);
+                cudaEventRecord(e1, b->stream);
+                if (e != cudaSuccess) return CCMC_ERR_CUDA;
+                batch_after_step(b);
+                k++;
+                ccmc_status st = batch_boundaries(b);
+                if (st != CCMC_OK) return st;
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = sh;
+                }
+            }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (k >= 8) {
+            b->sh = best;
+            b->tuned = true;
+        }
+    }
+    for (; k < nsteps; k++) {
+        if (b->tuned) {
+            if (!b->graph) {
+                i64 before[8];
+                for (int i = 0; i < 8; i++) before[i] = b->launches[i];
+                cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+                if (e != cudaSuccess) return CCMC_ERR_CUDA;
+                e = batch_launch(b, b->sh);
+                cudaGraph_t g = nullptr;
+                cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+                if (e == cudaSuccess) e = e2;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+                if (g) cudaGraphDestroy(g);
+                for (int i = 0; i < 8; i++) {
+                    b->graph_launches[i] = b->launches[i] - before[i];
+                    b->launches[i] = before[i];
+                }
+                if (e != cudaSuccess) {
+                    b->graph = nullptr;
+                    return CCMC_ERR_CUDA;
+                }
+            }
+            if (b->profile) {
+                if (batch_launch(b, b->sh) != cudaSuccess) return CCMC_ERR_CUDA;
+            } else {
+                if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return CCMC_ERR_CUDA;
+                for (int i = 0; i < 8; i++) b->launches[i] += b->graph_launches[i];
+            }
+        } else {
+            if (batch_launch(b, b->sh) != cudaSuccess) return CCMC_ERR_CUDA;
+        }
+        batch_after_step(b);
+        ccmc_status st = batch_boundaries(b);
+        if (st != CCMC_OK) return st;
+    }
+    return CCMC_OK;
+}
+
+ccmc_status ccmc_batch_profile(ccmc_batch *b, int32_t enable)
+{
+    if (!b) return CCMC_ERR_ARG;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return CCMC_ERR_CUDA;
+    if (enable && b->events.empty()) {
+        b->events.resize(8 * b->groups.size());
+        for (cudaEvent_t &e : b->events)
+            if (cudaEventCreate(&e) != cudaSuccess) return CCMC_ERR_CUDA;
+    }
+    b->profile = enable != 0;
+    for (int i = 0; i < 8; i++) {
+        b->phase_ms[i] = 0.0;
+        b->launch0[i] = b->launches[i];
+    }
+    return CCMC_OK;
+}
+
+ccmc_status ccmc_batch_phase_times(ccmc_batch *b, double *ms, int64_t *launches, int32_t nphases,
+                                   int64_t *total_launches)
+{
+    if (!b || nphases < 0) return CCMC_ERR_ARG;
+    for (int ph = 0; ph < nphases && ph < NPHASES; ph++) {
+        if (ms) ms[ph] = b->phase_ms[ph];
+        if (launches) launches[ph] = b->launches[ph] - b->launch0[ph];
+    }
+    if (total_launches) {
+        i64 t = 0;
+        for (int ph = 0; ph < NPHASES; ph++) t += b->launches[ph];
+        *total_launches = t;
+    }
+    return CCMC_OK;
+}
+
+ccmc_status ccmc_batch_info(ccmc_batch *b, int32_t *work_blocks, int32_t *digit_bits, int32_t *groups)
+{
+    if (!b) return CCMC_ERR_ARG;
+    if (work_blocks) *work_blocks = b->sh.work_grid;
+    if (digit_bits) *digit_bits = b->sh.digit_bits;
+    if (groups) *groups = (int32_t)b->groups.size();
+    return CCMC_OK;
+}
+
+void ccmc_batch_free(ccmc_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+    for (void *p : b->blocks) cudaFree(p);
+    if (b->h_rec) cudaFreeHost(b->h_rec);
+    if (b->h_err) cudaFreeHost(b->h_err);
+    if (b->h_shift) cudaFreeHost(b->h_shift);
+    delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,46 @@
+"""Batched form: replicas of different systems stepped in one launch per
+phase must be bit-identical to the same contexts stepped alone."""
+import numpy as np
+import pytest
+
+from ccmc_inputs import batched_replicas, molecule_integrals, workload
+
+pytestmark = pytest.mark.gpu
+
+
+def _replica_specs():
+    h1, eri = molecule_integrals(norb=8, nocc=3, seed=5, scale=0.1)
+    reps = batched_replicas(16)
+    chosen = [reps[0], reps[5], reps[10], reps[15]]            # M = 38, 54, 66, 114 (one and two words)
+    chosen += [dict(r, lmax=3, replica=100 + i) for i, r in enumerate(batched_replicas(16)[1:3])]   # CCSDT
+    chosen.append(workload("ueg14_m114_ccsdt_fnc_ms", target_pop=2e4, replica=7))          # FNC + multi-spawn
+    chosen.append(workload("ueg14_m38_ccsd", precision="fp32", replica=8))                  # FP32 group
+    chosen.append(dict(kind="generic", nel=6, norb=8, nso=16, lmax=3, h1=h1, eri=eri, tau=0.01, target_pop=3000.0,
+                       d0_init=400.0, shift_a=10, zeta=0.05, spawn_cutoff=2.0 ** -7, a_thresh=1.0, seed=3,
+                       replica=9, fnc=0, multispawn=0))
+    return chosen
+
+
+def test_batched_equals_plain(ccmc_lib=None):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA")
+    import paper_1807_03749_gb300 as ccmc
+
+    specs = _replica_specs()
+    stream = torch.cuda.Stream()
+    batch_ctx = [ccmc.from_workload(w) for w in specs]
+    plain_ctx = [ccmc.from_workload(w) for w in specs]
+    b = ccmc.Batch(batch_ctx, stream.cuda_stream)
+    for chunk in (13, 27, 40):          # the first call tunes on its first steps
+        b.step(chunk)
+        for c in plain_ctx:
+            c.step(chunk)
+        for cb, cp in zip(batch_ctx, plain_ctx):
+            rb, rp = cb.records(), cp.records()
+            assert rb == rp
+            for x, y in zip(cb.get_list(), cp.get_list()):
+                assert np.array_equal(x, y)
+            assert cb.get_state() == cp.get_state()
+    info = b.info()
+    assert info["groups"] == 3 and info["work_blocks"] in (8, 16, 32, 64) and info["digit_bits"] in (6, 8)
