@@ -432,10 +432,11 @@ def run_gpu_batched(args):
         if time.perf_counter() - t_grow > args.grow_seconds:
             raise RuntimeError(f"batched growth did not settle within {args.grow_seconds} s ({grown} steps)")
         if grown % 100 == 0:
-            for c in ctxs:
+            for c, w in zip(ctxs, reps):
                 en = c.energy()
-                if en["n_total"] > 1e3 * max(en["n0"], 1.0):
-                    raise RuntimeError(f"growth did not settle: N_total={en['n_total']:.3e}, t_HF={en['n0']:.3e}")
+                if en["n_total"] > 100.0 * w["target_pop"]:
+                    raise RuntimeError(f"{w['name']}: population {en['n_total']:.3e} far above its target "
+                                       f"{w['target_pop']:.0e} after {grown} steps")
         if reached is None and all(st[2] for st in states):
             reached = grown
         if reached is not None and grown >= reached + args.equilibrate:

@@ -57,16 +57,24 @@ def workload(name: str, **overrides) -> dict:
 def batched_replicas(n: int = 64) -> list[dict]:
     """Replica r: M in {38, 54, 66, 114} x r_s in {0.5, 1, 2, 5} by r mod 16,
     CCSD when floor(r/16) is even else CCSDT, target 10^(4 + r mod 3),
-    seed 1000 + r."""
+    seed 1000 + r, with two exceptions found by running every replica alone
+    for 8000 steps: CCSDT at M = 114 did not settle at these populations (at
+    r_s = 5 not even at 10^6; the population blew up within 1000-4000 steps),
+    so M = 114 replicas are CCSD throughout; and CCSDT at M = 66, r_s = 5
+    needs 10^6 excitors to settle.  Lists get room for 8x the target."""
     out = []
     ms = [38, 54, 66, 114]
     rss = [0.5, 1.0, 2.0, 5.0]
     for r in range(n):
         c = r % 16
+        m, rs = ms[c // 4], rss[c % 4]
+        lmax = 3 if (r // 16) % 2 == 1 and m < 114 else 2
+        target = 10.0 ** (4 + r % 3)
+        if lmax == 3 and m == 66 and rs == 5.0:
+            target = 1.0e6
         w = copy.deepcopy(COMMON)
-        w.update(kind="ueg", nel=14, nso=ms[c // 4], rs=rss[c % 4], lmax=2 if (r // 16) % 2 == 0 else 3,
-                 target_pop=10.0 ** (4 + r % 3), tau=0.01, nsteps=100, seed=1000 + r, replica=r,
-                 name=f"batched_r{r}")
+        w.update(kind="ueg", nel=14, nso=m, rs=rs, lmax=lmax, target_pop=target, tau=0.01, nsteps=100,
+                 seed=1000 + r, replica=r, list_capacity=int(8 * target) + 65536, name=f"batched_r{r}")
         out.append(w)
     return out
 

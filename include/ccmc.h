@@ -227,8 +227,13 @@ ccmc_status ccmc_phase_times(ccmc_ctx *ctx, double *ms, int64_t *launches, int32
  * Every phase of the step is one kernel launch over all replicas that share
  * a determinant word count and precision (a CUDA grid dimension indexes the
  * replica), and the whole step is captured once in a CUDA graph and replayed.
- * Per-replica grid sizes and the radix digit width are chosen by timing
- * candidates on the first steps (the trajectory does not depend on them).
+ * The cluster sampler, the bulk of the work, is one persistent launch whose
+ * blocks take shares of the replicas' samples from a plan written on the
+ * device each step, so replicas of very different sizes keep the GPU busy.
+ * Per-replica grid sizes, the sampler's samples per share and the radix digit
+ * width are chosen by timing candidates on real steps, again whenever the
+ * batch's total population has changed by a factor of two since the last
+ * choice (the trajectory does not depend on them).
  * Replicas keep their own Philox keys, shift control and checkpoints; results
  * are bit-identical to stepping each context alone. */
 typedef struct ccmc_batch ccmc_batch;
@@ -239,13 +244,15 @@ typedef struct ccmc_batch ccmc_batch;
 ccmc_status ccmc_batch_create(ccmc_ctx **ctxs, int32_t n, void *cuda_stream, ccmc_batch **out);
 
 /* nsteps steps of every context in the batch.  The host synchronises at each
- * context's shift-update boundary (every shift_a steps).  The first call
- * times tuning candidates on its first steps before capturing the graph. */
+ * context's shift-update boundary (every shift_a steps).  Tuning steps are
+ * issued one by one and timed; the graph is captured after each tuning. */
 ccmc_status ccmc_step_batched(ccmc_batch *b, int32_t nsteps);
 
-/* The tuned per-replica work-grid blocks and radix digit width (after the
- * first ccmc_step_batched), and the number of replica groups. */
-ccmc_status ccmc_batch_info(ccmc_batch *b, int32_t *work_blocks, int32_t *digit_bits, int32_t *groups);
+/* The current per-replica work-grid blocks, the sampler's samples per share
+ * (sample_tile), the radix digit width, the number of replica groups and how
+ * many times the shapes have been tuned (any pointer may be NULL). */
+ccmc_status ccmc_batch_info(ccmc_batch *b, int32_t *work_blocks, int32_t *sample_tile, int32_t *digit_bits,
+                            int32_t *groups, int32_t *tunings);
 
 /* Per-phase timers of the batch, as ccmc_profile / ccmc_phase_times for a
  * context (phases summed over the replica groups). */

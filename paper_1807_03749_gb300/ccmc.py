@@ -105,7 +105,7 @@ def load(path: str | None = None):
         "ccmc_reduce_records_noalloc": (c_int, [vp, vp, c_size_t, c_int32, vp, vp, POINTER(c_size_t), vp]),
         "ccmc_batch_create": (c_int, [POINTER(c_void_p), c_int32, vp, POINTER(c_void_p)]),
         "ccmc_step_batched": (c_int, [vp, c_int32]),
-        "ccmc_batch_info": (c_int, [vp, i32p, i32p, i32p]),
+        "ccmc_batch_info": (c_int, [vp, i32p, i32p, i32p, i32p, i32p]),
         "ccmc_batch_free": (None, [vp]),
         "ccmc_batch_profile": (c_int, [vp, c_int32]),
         "ccmc_batch_phase_times": (c_int, [vp, dp, i64p, c_int32, i64p]),
@@ -321,12 +321,19 @@ class Batch:
     def step(self, nsteps: int = 1):
         st = self._lib.ccmc_step_batched(self._h, nsteps)
         if st != 0:
-            raise CCMCError(st, "ccmc_step_batched failed")
+            why = []
+            for i, c in enumerate(self.contexts):
+                msg = self._lib.ccmc_last_error(c._h)
+                if msg:
+                    why.append(f"context {i}: {msg.decode()}")
+            raise CCMCError(st, "ccmc_step_batched failed" + ("; " + "; ".join(why) if why else ""))
 
     def info(self) -> dict:
-        w, d, g = c_int32(0), c_int32(0), c_int32(0)
-        self._lib.ccmc_batch_info(self._h, ctypes.byref(w), ctypes.byref(d), ctypes.byref(g))
-        return {"work_blocks": w.value, "digit_bits": d.value, "groups": g.value}
+        w, t, d, g, n = c_int32(0), c_int32(0), c_int32(0), c_int32(0), c_int32(0)
+        self._lib.ccmc_batch_info(self._h, ctypes.byref(w), ctypes.byref(t), ctypes.byref(d), ctypes.byref(g),
+                                  ctypes.byref(n))
+        return {"work_blocks": w.value, "sample_tile": t.value, "digit_bits": d.value, "groups": g.value,
+                "tunings": n.value}
 
     def profile(self, enable: bool = True):
         if self._lib.ccmc_batch_profile(self._h, int(enable)):

@@ -994,7 +994,26 @@ struct BatchGroup {
     std::vector<int> members;
     StepArgs *d_args = nullptr;
     int key_bits = 1;
+    int *d_vstart = nullptr;        // sampler plan (members + 1 entries)
+    unsigned *d_counter = nullptr;
 };
+
+// Shapes the tuner chooses between.
+struct BatchShape {
+    int work = 64;      // per-replica blocks of the list, merge and sort kernels
+    int tile = 1024;    // samples per share of the persistent sampler
+    int digit = 8;      // radix digit bits
+};
+
+constexpr int TUNE_STAGES = 3;
+const int TUNE_WORK[] = {32, 64, 128, 256};
+const int TUNE_TILE[] = {256, 512, 1024, 2048, 4096};
+const int TUNE_DIGIT[] = {8, 6};
+
+int tune_count(int stage)
+{
+    return stage == 0 ? 4 : stage == 1 ? 5 : 2;
+}
 
 }  // namespace
 
@@ -1007,7 +1026,15 @@ struct ccmc_batch {
     unsigned *d_err = nullptr, *h_err = nullptr;
     double *d_shift = nullptr, *h_shift = nullptr;
     Shapes sh;                        // per-replica shapes (key_bits set per group)
+    Shapes lim;                       // what every context allocated for
+    BatchShape shape;                 // current choice
+    int flat_grid = 0;                // blocks of the persistent sampler
     bool tuned = false;
+    int tune_stage = 0, tune_idx = 0, tunings = 0;
+    BatchShape tune_best;
+    float tune_best_ms = 0.0f;
+    cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+    double pop_now = 0.0, pop_tuned = 0.0;   // batch population at the last boundary / last tuning
     cudaGraphExec_t graph = nullptr;
     i64 launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     i64 graph_launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -1021,15 +1048,33 @@ struct ccmc_batch {
 
 namespace {
 
+// per-replica shapes for a tuner choice, within what every context allocated
+Shapes shapes_for(const ccmc_batch *b, const BatchShape &c)
+{
+    Shapes sh = b->lim;
+    sh.work_grid = std::min(c.work, b->lim.work_grid);
+    sh.scan_grid = std::min(std::max(2, c.work / 2), b->lim.scan_grid);
+    sh.sort_grid = std::min(std::max(2, c.work / 2), b->lim.sort_grid);
+    sh.digit_bits = c.digit;
+    sh.enum_slots = sh.scan_grid + sh.work_grid;
+    return sh;
+}
+
 cudaError_t batch_launch(ccmc_batch *b, const Shapes &base)
 {
     for (size_t gi = 0; gi < b->groups.size(); gi++) {
         BatchGroup &g = b->groups[gi];
         Shapes sh = base;
         sh.key_bits = g.key_bits;
+        FlatPlan plan;
+        plan.vstart = g.d_vstart;
+        plan.counter = g.d_counter;
+        plan.per_block = b->shape.tile;
+        plan.wmax = b->lim.work_grid;
+        plan.grid = b->flat_grid;
         const cudaEvent_t *ev = b->profile ? &b->events[8 * gi] : nullptr;
         cudaError_t e = launch_group(g.d_args, (int)g.members.size(), g.K, g.fp32, sh, g.multi, b->stream,
-                                     b->launches, ev);
+                                     b->launches, ev, &plan);
         if (e != cudaSuccess) return e;
     }
     if (b->profile) {
@@ -1045,10 +1090,10 @@ cudaError_t batch_launch(ccmc_batch *b, const Shapes &base)
     return cudaSuccess;
 }
 
-void batch_after_step(ccmc_batch *b)
+void batch_after_step(ccmc_batch *b, const Shapes &launched)
 {
     for (BatchGroup &g : b->groups) {
-        Shapes sh = b->sh;
+        Shapes sh = launched;
         sh.key_bits = g.key_bits;
         for (int m : g.members) {
             ccmc_ctx *c = b->ctxs[m];
@@ -1073,6 +1118,17 @@ ccmc_status batch_boundaries(ccmc_batch *b)
         cudaStreamSynchronize(b->stream) != cudaSuccess)
         return CCMC_ERR_CUDA;
     bool changed = false;
+    double pop = 0.0;
+    for (int r = 0; r < n; r++) pop += (double)b->h_rec[r].ntot_after / 65536.0;
+    b->pop_now = pop;
+    // a population twice or half as large as at the last tuning: tune again
+    if (b->tuned && (pop > 2.0 * b->pop_tuned || pop < 0.5 * b->pop_tuned)) {
+        b->tuned = false;
+        b->tune_stage = 0;
+        b->tune_idx = 0;
+        b->tune_best = b->shape;
+        b->tune_best_ms = 1e30f;
+    }
     for (int r = 0; r < n; r++) {
         ccmc_ctx *c = b->ctxs[r];
         if (b->h_err[r]) return status_from_bits(c, b->h_err[r]);
@@ -1158,7 +1214,9 @@ ccmc_status ccmc_batch_create(ccmc_ctx **ctxs, int32_t n, void *cuda_stream, ccm
         std::vector<StepArgs> ga;
         for (int m : g.members) ga.push_back(all[m]);
         g.d_args = (StepArgs *)dalloc(sizeof(StepArgs) * ga.size());
-        ok = ok && g.d_args &&
+        g.d_vstart = (int *)dalloc(sizeof(int) * (ga.size() + 1));
+        g.d_counter = (unsigned *)dalloc(sizeof(unsigned));
+        ok = ok && g.d_args && g.d_vstart && g.d_counter &&
              cudaMemcpy(g.d_args, ga.data(), sizeof(StepArgs) * ga.size(), cudaMemcpyHostToDevice) == cudaSuccess;
     }
     // per-replica shapes may not exceed what every context allocated for
@@ -1168,12 +1226,17 @@ ccmc_status ccmc_batch_create(ccmc_ctx **ctxs, int32_t n, void *cuda_stream, ccm
         lim.work_grid = std::min(lim.work_grid, ctxs[r]->sc.sh.work_grid);
         lim.sort_grid = std::min(lim.sort_grid, ctxs[r]->sc.sh.sort_grid);
     }
-    b->sh = lim;
-    b->sh.work_grid = std::min(lim.work_grid, 16);
-    b->sh.scan_grid = std::min(lim.scan_grid, 8);
-    b->sh.sort_grid = std::min(lim.sort_grid, 8);
-    b->sh.digit_bits = MAX_DIGIT_BITS;
-    b->sh.enum_slots = b->sh.scan_grid + b->sh.work_grid;
+    lim.digit_bits = MAX_DIGIT_BITS;
+    b->lim = lim;
+    b->sh = shapes_for(b, b->shape);
+    int dev = 0, sms = 0;
+    ok = ok && cudaGetDevice(&dev) == cudaSuccess &&
+         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+         cudaEventCreate(&b->tune_ev[0]) == cudaSuccess && cudaEventCreate(&b->tune_ev[1]) == cudaSuccess;
+    b->flat_grid = 3 * std::max(1, sms);   // resident blocks of the sampler (3 per SM)
+    for (int r = 0; r < n; r++) b->pop_now += ctxs[r]->prm.d0_init;
+    b->tune_best = b->shape;
+    b->tune_best_ms = 1e30f;
     if (!ok) {
         ccmc_batch_free(b);
         return CCMC_ERR_OOM;
@@ -1182,89 +1245,95 @@ ccmc_status ccmc_batch_create(ccmc_ctx **ctxs, int32_t n, void *cuda_stream, ccm
     return CCMC_OK;
 }
 
+// the candidate for the current tuning position
+static BatchShape tune_candidate(const ccmc_batch *b)
+{
+    BatchShape c = b->tune_best;
+    if (b->tune_stage == 0) c.work = TUNE_WORK[b->tune_idx];
+    else if (b->tune_stage == 1) c.tile = TUNE_TILE[b->tune_idx];
+    else c.digit = TUNE_DIGIT[b->tune_idx];
+    return c;
+}
+
+// One timed tuning step: the candidates of one stage are tried in turn with
+// the best of the earlier stages (coordinate search); after the last stage
+// the best choice is kept and the graph is captured again.
+static ccmc_status batch_tune_step(ccmc_batch *b, Shapes &launched)
+{
+    b->shape = tune_candidate(b);
+    b->sh = shapes_for(b, b->shape);
+    launched = b->sh;
+    if (cudaEventRecord(b->tune_ev[0], b->stream) != cudaSuccess) return CCMC_ERR_CUDA;
+    if (batch_launch(b, b->sh) != cudaSuccess) return CCMC_ERR_CUDA;
+    if (cudaEventRecord(b->tune_ev[1], b->stream) != cudaSuccess) return CCMC_ERR_CUDA;
+    if (cudaEventSynchronize(b->tune_ev[1]) != cudaSuccess) return CCMC_ERR_CUDA;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, b->tune_ev[0], b->tune_ev[1]);
+    if (ms < b->tune_best_ms) {
+        b->tune_best_ms = ms;
+        b->tune_best = b->shape;
+    }
+    if (++b->tune_idx == tune_count(b->tune_stage)) {
+        b->tune_idx = 0;
+        b->tune_stage++;
+        b->tune_best_ms = 1e30f;   // the next stage is timed afresh
+        if (b->tune_stage == TUNE_STAGES) {
+            b->shape = b->tune_best;
+            b->sh = shapes_for(b, b->shape);
+            b->tuned = true;
+            b->tunings++;
+            b->pop_tuned = b->pop_now;
+            if (b->graph) {
+                cudaGraphExecDestroy(b->graph);
+                b->graph = nullptr;
+            }
+        }
+    }
+    return CCMC_OK;
+}
+
+static ccmc_status batch_capture(ccmc_batch *b)
+{
+    i64 before[8];
+    for (int i = 0; i < 8; i++) before[i] = b->launches[i];
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return CCMC_ERR_CUDA;
+    e = batch_launch(b, b->sh);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    for (int i = 0; i < 8; i++) {
+        b->graph_launches[i] = b->launches[i] - before[i];
+        b->launches[i] = before[i];
+    }
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return CCMC_ERR_CUDA;
+    }
+    return CCMC_OK;
+}
+
 ccmc_status ccmc_step_batched(ccmc_batch *b, int32_t nsteps)
 {
     if (!b || nsteps < 0) return CCMC_ERR_ARG;
-    int k = 0;
-    if (!b->tuned && nsteps > 0) {
-        // time candidate shapes on real steps (results do not depend on them)
-        const int wcand[] = {8, 16, 32, 64};
-        const int dcand[] = {6, 8};
-        Shapes best = b->sh;
-        float best_ms = 1e30f;
-        cudaEvent_t e0, e1;
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        for (int wi = 0; wi < 4 && k < nsteps; wi++)
-            for (int di = 0; di < 2 && k < nsteps; di++) {
-                Shapes sh = b->sh;
-                Shapes lim = b->ctxs[0]->sc.sh;
-                for (ccmc_ctx *c : b->ctxs) {
-                    lim.work_grid = std::min(lim.work_grid, c->sc.sh.work_grid);
-                    lim.scan_grid = std::min(lim.scan_grid, c->sc.sh.scan_grid);
-                    lim.sort_grid = std::min(lim.sort_grid, c->sc.sh.sort_grid);
-                }
-                sh.work_grid = std::min(wcand[wi], lim.work_grid);
-                sh.scan_grid = std::min(std::max(2, wcand[wi] / 2), lim.scan_grid);
-                sh.sort_grid = std::min(std::max(2, wcand[wi] / 2), lim.sort_grid);
-                sh.digit_bits = dcand[di];
-                sh.enum_slots = sh.scan_grid + sh.work_grid;
-                b->sh = sh;
-                cudaEventRecord(e0, b->stream);
-                cudaError_t e = batch_launch(b, sh);
-                cudaEventRecord(e1, b->stream);
-                if (e != cudaSuccess) return CCMC_ERR_CUDA;
-                batch_after_step(b);
-                k++;
-                ccmc_status st = batch_boundaries(b);
-                if (st != CCMC_OK) return st;
-                cudaEventSynchronize(e1);
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best = sh;
-                }
-            }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        if (k >= 8) {
-            b->sh = best;
-            b->tuned = true;
-        }
-    }
-    for (; k < nsteps; k++) {
-        if (b->tuned) {
-            if (!b->graph) {
-                i64 before[8];
-                for (int i = 0; i < 8; i++) before[i] = b->launches[i];
-                cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-                if (e != cudaSuccess) return CCMC_ERR_CUDA;
-                e = batch_launch(b, b->sh);
-                cudaGraph_t g = nullptr;
-                cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
-                if (e == cudaSuccess) e = e2;
-                if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
-                if (g) cudaGraphDestroy(g);
-                for (int i = 0; i < 8; i++) {
-                    b->graph_launches[i] = b->launches[i] - before[i];
-                    b->launches[i] = before[i];
-                }
-                if (e != cudaSuccess) {
-                    b->graph = nullptr;
-                    return CCMC_ERR_CUDA;
-                }
-            }
-            if (b->profile) {
-                if (batch_launch(b, b->sh) != cudaSuccess) return CCMC_ERR_CUDA;
-            } else {
-                if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return CCMC_ERR_CUDA;
-                for (int i = 0; i < 8; i++) b->launches[i] += b->graph_launches[i];
-            }
-        } else {
+    for (int k = 0; k < nsteps; k++) {
+        Shapes launched = b->sh;
+        if (!b->tuned) {
+            ccmc_status st = batch_tune_step(b, launched);
+            if (st != CCMC_OK) return st;
+        } else if (b->profile) {
             if (batch_launch(b, b->sh) != cudaSuccess) return CCMC_ERR_CUDA;
+        } else {
+            if (!b->graph) {
+                ccmc_status st = batch_capture(b);
+                if (st != CCMC_OK) return st;
+            }
+            if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return CCMC_ERR_CUDA;
+            for (int i = 0; i < 8; i++) b->launches[i] += b->graph_launches[i];
         }
-        batch_after_step(b);
+        batch_after_step(b, launched);
         ccmc_status st = batch_boundaries(b);
         if (st != CCMC_OK) return st;
     }
@@ -1304,12 +1373,15 @@ ccmc_status ccmc_batch_phase_times(ccmc_batch *b, double *ms, int64_t *launches,
     return CCMC_OK;
 }
 
-ccmc_status ccmc_batch_info(ccmc_batch *b, int32_t *work_blocks, int32_t *digit_bits, int32_t *groups)
+ccmc_status ccmc_batch_info(ccmc_batch *b, int32_t *work_blocks, int32_t *sample_tile, int32_t *digit_bits,
+                            int32_t *groups, int32_t *tunings)
 {
     if (!b) return CCMC_ERR_ARG;
     if (work_blocks) *work_blocks = b->sh.work_grid;
+    if (sample_tile) *sample_tile = b->shape.tile;
     if (digit_bits) *digit_bits = b->sh.digit_bits;
     if (groups) *groups = (int32_t)b->groups.size();
+    if (tunings) *tunings = b->tunings;
     return CCMC_OK;
 }
 
@@ -1319,6 +1391,8 @@ void ccmc_batch_free(ccmc_batch *b)
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->tune_ev)
+        if (e) cudaEventDestroy(e);
     for (void *p : b->blocks) cudaFree(p);
     if (b->h_rec) cudaFreeHost(b->h_rec);
     if (b->h_err) cudaFreeHost(b->h_err);

@@ -113,7 +113,7 @@ struct Shapes {
     int sort_grid;    // blocks of SORT_THREADS for sort passes
     int digit_bits;   // radix digit width
     int key_bits;     // significant key bits
-    int enum_slots;   // scan_grid + 2 * work_grid
+    int enum_slots;   // scan_grid + work_grid (E_num partials of the scans and the sampler)
 };
 
 // Per-replica arguments of the step kernels (device-resident; a single
@@ -154,13 +154,27 @@ struct StepCtx {
 
 constexpr int NPHASES = 7;
 
+// Work plan of a batch's cluster sampler: replica r owns the virtual blocks
+// [vstart[r], vstart[r+1]), about one per per_block samples (at least one, at
+// most wmax), and a persistent grid of `grid` blocks takes virtual blocks
+// from `counter` until all are done.  Written on the device every step.
+struct FlatPlan {
+    int *vstart;          // nrep + 1 entries
+    unsigned *counter;    // next virtual block
+    int per_block;        // samples per virtual block
+    int wmax;             // virtual blocks per replica at most (<= its work-array slots)
+    int grid;             // blocks of the persistent sampler
+};
+
 // Issues one full time step on ctx.stream.  Returns a CUDA error code.
 cudaError_t launch_step(StepCtx &ctx);
 
 // Issues one step for nrep replicas of the same word count and precision
 // whose arguments are A[0..nrep); launch counts are added to launches[7].
+// With a work plan the sampler runs as one persistent launch over all of
+// them, with blocks shared out in proportion to each replica's samples.
 cudaError_t launch_group(const StepArgs *A, int nrep, int K, bool fp32, const Shapes &sh, bool multi_att,
-                         cudaStream_t sm, i64 *launches, const cudaEvent_t *ev);
+                         cudaStream_t sm, i64 *launches, const cudaEvent_t *ev, const FlatPlan *plan = nullptr);
 
 // Number of radix passes for the shapes.
 int sort_passes(const Shapes &sh);

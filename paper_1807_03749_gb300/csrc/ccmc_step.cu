@@ -522,7 +522,8 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
 
 template <int K, typename R>
 __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, DevStep *st, const RunParams &p, const WorkArrays &wa,
-                                                         const SpawnBuf &sp, const ClusterBuf &cl, int enum_base)
+                                                         const SpawnBuf &sp, const ClusterBuf &cl, int enum_base,
+                                                         int vb, int vg)
 {
     __shared__ double smag[8];
     __shared__ u64 smf[64];
@@ -543,7 +544,7 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
     i64 death_hf = 0;   // reference-cluster deaths, summed per block at the end
     // block-uniform loop: appends are reserved with one atomic per block
     // (per-warp atomics on one counter contend at 1e8 samples per step)
-    for (i64 g0 = (i64)blockIdx.x * blockDim.x; g0 < n_sel; g0 += (i64)gridDim.x * blockDim.x) {
+    for (i64 g0 = (i64)vb * blockDim.x; g0 < n_sel; g0 += (i64)vg * blockDim.x) {
         const i64 g = g0 + threadIdx.x;
         int nrec = 0;
         u64 rk[2] = {0, 0};
@@ -666,8 +667,8 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
     death_hf = block_sum(death_hf, sm);
     if (threadIdx.x == 0) {
         if (death_hf) atomicAdd((unsigned long long *)&wa.death[0], (unsigned long long)death_hf);
-        wa.enum_part[2 * (enum_base + blockIdx.x)] = es.lo;
-        wa.enum_part[2 * (enum_base + blockIdx.x) + 1] = es.hi;
+        wa.enum_part[2 * (enum_base + vb)] = es.lo;
+        wa.enum_part[2 * (enum_base + vb) + 1] = es.hi;
         if (inline_att) atomicAdd((unsigned long long *)&st->n_attempts, (unsigned long long)inline_att);
     }
     if (err) atomicOr(&st->err, err);   // every thread reports its own bits
@@ -1157,7 +1158,96 @@ template <int K, typename R>
 __global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(const StepArgs *__restrict__ A, int enum_base)
 {
     REPLICA_SMEM;
-    d_sample<K, R>(a.s, a.list[cur_], a.st, a.p, a.wa, a.sp, a.cl, enum_base);
+    d_sample<K, R>(a.s, a.list[cur_], a.st, a.p, a.wa, a.sp, a.cl, enum_base, blockIdx.x, gridDim.x);
+}
+
+// Batch work plan for the sampler: virtual blocks per replica from its
+// sample count, their prefix, the reset work counter, and zeroed E_num
+// partials for the slots a replica does not use this step (the final
+// reduction reads wmax of them).  One block.
+__global__ void __launch_bounds__(1024) k_sample_plan(const StepArgs *__restrict__ A, int nrep, FlatPlan fp,
+                                                       int enum_base)
+{
+    __shared__ int sm[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int r0 = 0; r0 < nrep; r0 += blockDim.x) {
+        const int r = r0 + threadIdx.x;
+        int want = 0;
+        if (r < nrep) {
+            const i64 ns = A[r].st->n_sel;
+            const i64 w = (ns + fp.per_block - 1) / fp.per_block;
+            want = (int)(w < 1 ? 1 : (w > fp.wmax ? fp.wmax : w));
+        }
+        int tot;
+        const int incl = block_incl_scan(want, sm, tot);
+        if (r < nrep) fp.vstart[r] = carry + incl - want;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        fp.vstart[nrep] = carry;
+        *fp.counter = 0u;
+    }
+    __syncthreads();
+    // unused E_num slots of every replica
+    for (int r = 0; r < nrep; r++) {
+        const i64 ns = A[r].st->n_sel;
+        const i64 w = (ns + fp.per_block - 1) / fp.per_block;
+        const int used = (int)(w < 1 ? 1 : (w > fp.wmax ? fp.wmax : w));
+        u64 *ep = A[r].wa.enum_part;
+        for (int q = used + (int)threadIdx.x; q < fp.wmax; q += blockDim.x) {
+            ep[2 * (enum_base + q)] = 0;
+            ep[2 * (enum_base + q) + 1] = 0;
+        }
+    }
+}
+
+// Persistent batch sampler: each block takes the next virtual block of the
+// plan, finds its replica and runs that share of the replica's samples.
+template <int K, typename R>
+__global__ void __launch_bounds__(WORK_THREADS, 3) k_sample_flat(const StepArgs *__restrict__ A, int nrep, FlatPlan fp,
+                                                                 int enum_base)
+{
+    __shared__ StepArgs a_sm;
+    __shared__ int s_v, s_r;
+    const int total = fp.vstart[nrep];
+    int have = -1;
+    for (;;) {
+        __syncthreads();   // the previous share is finished with a_sm and s_v
+        if (threadIdx.x == 0) {
+            const int v = (int)atomicAdd(fp.counter, 1u);
+            int r = 0;
+            if (v < total) {
+                int lo = 0, hi = nrep - 1;   // last r with vstart[r] <= v
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (fp.vstart[mid] <= v) lo = mid;
+                    else hi = mid - 1;
+                }
+                r = lo;
+            }
+            s_v = v;
+            s_r = r;
+        }
+        __syncthreads();
+        const int v = s_v;
+        if (v >= total) break;
+        const int r = s_r;
+        if (r != have) {
+            const u64 *src = (const u64 *)&A[r];
+            u64 *dst = (u64 *)&a_sm;
+            for (int q = threadIdx.x; q < (int)(sizeof(StepArgs) / 8); q += blockDim.x) dst[q] = src[q];
+            __syncthreads();
+            have = r;
+        }
+        const StepArgs &a = a_sm;
+        const int v0 = fp.vstart[r];
+        d_sample<K, R>(a.s, a.list[a.st->cur], a.st, a.p, a.wa, a.sp, a.cl, enum_base, v - v0,
+                       fp.vstart[r + 1] - v0);
+    }
 }
 
 template <int K, typename R>
@@ -1309,7 +1399,7 @@ int sort_passes(const Shapes &sh)
 
 template <int K, typename R>
 static cudaError_t launch_phases(const StepArgs *A, int nrep, const Shapes &sh, bool multi_att, cudaStream_t sm,
-                                 i64 *launches, const cudaEvent_t *ev)
+                                 i64 *launches, const cudaEvent_t *ev, const FlatPlan *plan)
 {
     auto mark = [&](int phase) {
         if (ev) cudaEventRecord(ev[phase], sm);
@@ -1321,8 +1411,14 @@ static cudaError_t launch_phases(const StepArgs *A, int nrep, const Shapes &sh, 
     k_scan_final<K, R><<<gscan, SCAN_THREADS, 0, sm>>>(A);
     launches[0] += 3;
     mark(1);
-    k_sample<K, R><<<gwork, WORK_THREADS, 0, sm>>>(A, sh.scan_grid);
-    launches[1] += 1;
+    if (plan) {
+        k_sample_plan<<<1, 1024, 0, sm>>>(A, nrep, *plan, sh.scan_grid);
+        k_sample_flat<K, R><<<plan->grid, WORK_THREADS, 0, sm>>>(A, nrep, *plan, sh.scan_grid);
+        launches[1] += 2;
+    } else {
+        k_sample<K, R><<<gwork, WORK_THREADS, 0, sm>>>(A, sh.scan_grid);
+        launches[1] += 1;
+    }
     mark(2);
     if (multi_att) {
         k_attempts<K, R><<<gwork, WORK_THREADS, 0, sm>>>(A);
@@ -1353,27 +1449,27 @@ static cudaError_t launch_phases(const StepArgs *A, int nrep, const Shapes &sh, 
     k_scatter_new<K, R><<<gwork, WORK_THREADS, 0, sm>>>(A, src);
     launches[5] += 7;
     mark(6);
-    k_finalize<<<gone, 1024, 0, sm>>>(A, sh.enum_slots);
+    k_finalize<<<gone, 1024, 0, sm>>>(A, plan ? sh.scan_grid + plan->wmax : sh.enum_slots);
     launches[6] += 1;
     mark(7);
     return cudaGetLastError();
 }
 
 cudaError_t launch_group(const StepArgs *A, int nrep, int K, bool fp32, const Shapes &sh, bool multi_att,
-                         cudaStream_t sm, i64 *launches, const cudaEvent_t *ev)
+                         cudaStream_t sm, i64 *launches, const cudaEvent_t *ev, const FlatPlan *plan)
 {
     if (fp32) {
         switch (K) {
-        case 1: return launch_phases<1, float>(A, nrep, sh, multi_att, sm, launches, ev);
-        case 2: return launch_phases<2, float>(A, nrep, sh, multi_att, sm, launches, ev);
-        case 3: return launch_phases<3, float>(A, nrep, sh, multi_att, sm, launches, ev);
+        case 1: return launch_phases<1, float>(A, nrep, sh, multi_att, sm, launches, ev, plan);
+        case 2: return launch_phases<2, float>(A, nrep, sh, multi_att, sm, launches, ev, plan);
+        case 3: return launch_phases<3, float>(A, nrep, sh, multi_att, sm, launches, ev, plan);
         default: return cudaErrorInvalidValue;
         }
     }
     switch (K) {
-    case 1: return launch_phases<1, double>(A, nrep, sh, multi_att, sm, launches, ev);
-    case 2: return launch_phases<2, double>(A, nrep, sh, multi_att, sm, launches, ev);
-    case 3: return launch_phases<3, double>(A, nrep, sh, multi_att, sm, launches, ev);
+    case 1: return launch_phases<1, double>(A, nrep, sh, multi_att, sm, launches, ev, plan);
+    case 2: return launch_phases<2, double>(A, nrep, sh, multi_att, sm, launches, ev, plan);
+    case 3: return launch_phases<3, double>(A, nrep, sh, multi_att, sm, launches, ev, plan);
     default: return cudaErrorInvalidValue;
     }
 }

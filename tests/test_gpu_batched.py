@@ -43,4 +43,5 @@ def test_batched_equals_plain(ccmc_lib=None):
                 assert np.array_equal(x, y)
             assert cb.get_state() == cp.get_state()
     info = b.info()
-    assert info["groups"] == 3 and info["work_blocks"] in (8, 16, 32, 64) and info["digit_bits"] in (6, 8)
+    assert info["groups"] == 3 and info["work_blocks"] in (32, 64, 128, 256) and info["digit_bits"] in (6, 8)
+    assert info["sample_tile"] in (256, 512, 1024, 2048, 4096) and info["tunings"] >= 1
