@@ -55,7 +55,10 @@ typedef enum {
     CCMC_ERR_TIMEOUT = 5,         /* a bounded device wait gave up              */
     CCMC_ERR_NUMERIC = 6,         /* a weight left the fixed-point range        */
     CCMC_ERR_LIST_OVERFLOW = 7,   /* more occupied excitors than list_capacity  */
-    CCMC_ERR_STATE = 8            /* call not valid in the context's state      */
+    CCMC_ERR_STATE = 8,           /* call not valid in the context's state      */
+    CCMC_ERR_RUNAWAY = 9          /* population runaway: a step would need more
+                                     than max(64 x target_pop, 2^24) samples, or
+                                     spawning attempts; it was abandoned        */
 } ccmc_status;
 
 enum { CCMC_UEG = 0, CCMC_GENERIC = 1 };

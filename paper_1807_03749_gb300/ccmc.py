@@ -21,6 +21,7 @@ CCMC_FP64, CCMC_FP32 = 0, 1
 STATUS = {
     0: "CCMC_OK", 1: "CCMC_ERR_ARG", 2: "CCMC_ERR_CUDA", 3: "CCMC_ERR_OOM", 4: "CCMC_ERR_SPAWN_OVERFLOW",
     5: "CCMC_ERR_TIMEOUT", 6: "CCMC_ERR_NUMERIC", 7: "CCMC_ERR_LIST_OVERFLOW", 8: "CCMC_ERR_STATE",
+    9: "CCMC_ERR_RUNAWAY",
 }
 
 ALLOC_FN = CFUNCTYPE(c_void_p, c_size_t, c_void_p)
@@ -366,7 +367,8 @@ def from_workload(w: dict, **overrides) -> Context:
     if w["kind"] == "generic" and "h1" not in w:
         from ccmc_inputs import molecule_integrals
 
-        h1, eri = molecule_integrals(norb=w["norb"], nocc=w["nel"] // 2, seed=w.get("molecule_seed", 7))
+        h1, eri = molecule_integrals(norb=w["norb"], nocc=w["nel"] // 2, seed=w.get("molecule_seed", 7),
+                                     scale=w.get("eri_scale", 1.0))
         w["h1"], w["eri"] = h1, eri
     nso = w.get("nso", 2 * w.get("norb", 0))
     return Context(w["kind"], w["nel"], nso, w["lmax"], **{k: v for k, v in w.items()

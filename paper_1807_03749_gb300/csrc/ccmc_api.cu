@@ -242,6 +242,10 @@ ccmc_status cuda_fail(ccmc_ctx *c, cudaError_t e, const char *where)
 
 ccmc_status status_from_bits(ccmc_ctx *ctx, unsigned bits)
 {
+    // a runaway population overflows the buffers too; it is the cause to report
+    if (bits & ERRB_RUNAWAY)
+        return fail(ctx, CCMC_ERR_RUNAWAY, "population runaway: a step needed more than max(64 x target_pop, 2^24) "
+                                           "samples or spawning attempts");
     if (bits & ERRB_SPAWN_OVERFLOW) return fail(ctx, CCMC_ERR_SPAWN_OVERFLOW, "spawned particles exceeded spawn_capacity");
     if (bits & ERRB_CLUSTER_OVERFLOW) return fail(ctx, CCMC_ERR_SPAWN_OVERFLOW, "multi-spawn clusters exceeded capacity");
     if (bits & ERRB_LIST_OVERFLOW) return fail(ctx, CCMC_ERR_LIST_OVERFLOW, "occupied excitors exceeded list_capacity");
@@ -463,6 +467,14 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     rp.fnc = params->fnc ? 1 : 0;
     rp.multispawn = params->multispawn ? 1 : 0;
     rp.a_thresh_one = params->a_thresh == 1.0 ? 1 : 0;
+    {
+        // work per step beyond which a runaway population is reported
+        // instead of sampled: 64x the target, at least 2^24, at most 2^36
+        double cap = 64.0 * params->target_pop;
+        if (!(cap >= 16777216.0)) cap = 16777216.0;
+        if (cap > 68719476736.0) cap = 68719476736.0;
+        rp.work_cap = (i64)cap;
+    }
     {
         // integer rounding needs a cutoff of 0 or an exact power of two
         double c = params->spawn_cutoff;

@@ -36,7 +36,8 @@ enum : unsigned {
     ERRB_SPAWN_OVERFLOW = 1u,
     ERRB_NUMERIC = 2u,
     ERRB_LIST_OVERFLOW = 4u,
-    ERRB_CLUSTER_OVERFLOW = 8u
+    ERRB_CLUSTER_OVERFLOW = 8u,
+    ERRB_RUNAWAY = 16u
 };
 
 // Hamiltonian and generator tables as seen by the kernels (passed by value).

@@ -27,6 +27,7 @@ struct RunParams {
     int fnc, multispawn;
     int int_round;        // rounding decisions from the FP64 bit pattern (cutoff 0 or 2^k)
     int a_thresh_one;     // A_thresh == 1: floor(|A|) without a division
+    i64 work_cap;         // samples, visit attempts or cluster attempts per step beyond which the step is abandoned
     RoundSpec spawn_rs;   // spawn rounding (with the cutoff)
     RoundSpec death_rs;   // death rounding (no cutoff)
 };
@@ -66,6 +67,7 @@ struct DevStep {
     i64 kept_list, kept_new;
     i64 ntot_after;
     i64 n_start;        // list size at the start of the latest finished step
+    double cl_att;      // attempts of the buffered clusters (runaway check; exact below 2^53)
     unsigned err;
     int cur;            // list buffer holding the current list
 };

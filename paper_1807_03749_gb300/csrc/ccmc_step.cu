@@ -405,6 +405,12 @@ __device__ __forceinline__ void d_scan_top(const ListView &L, DevStep *st, const
         i64 an0 = n0 < 0 ? -n0 : n0;
         i64 ntot = an0 + tw;
         i64 n_sel = (ntot + 32768) >> 16;
+        // a runaway population: abandon the step instead of sampling it
+        if (n_sel > p.work_cap || (p.fnc && ta > p.work_cap)) {
+            atomicOr(&st->err, (unsigned)ERRB_RUNAWAY);
+            n_sel = 0;
+            ta = 0;
+        }
         st->n0 = n0;
         st->ntot = ntot;
         st->nex = tw;
@@ -446,6 +452,7 @@ __device__ __forceinline__ void d_scan_top(const ListView &L, DevStep *st, const
         }
         st->n_sp = 0;
         st->cl_packed = 0;
+        st->cl_att = 0.0;
         st->n_attempts = 0;
         st->n_keys = 0;
         st->kept_list = 0;
@@ -541,6 +548,7 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
     Fix128 es = {0, 0};
     unsigned err = 0;
     i64 inline_att = 0;
+    double cl_att = 0.0;   // attempts of the clusters this thread buffers
     i64 death_hf = 0;   // reference-cluster deaths, summed per block at the end
     // block-uniform loop: appends are reserved with one atomic per block
     // (per-warp atomics on one counter contend at 1e8 samples per step)
@@ -622,6 +630,11 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
                 if (p.multispawn) {
                     push = true;
                     catt = natt > 1 ? coef / (double)natt : coef;
+                    if (natt > p.work_cap) {   // runaway: the attempts kernel will not run them
+                        err |= ERRB_RUNAWAY;
+                        natt = p.work_cap + 1;
+                    }
+                    cl_att += (double)natt;
                 } else {
                     inline_att++;
                     R4 ra = draw(p.seed, p.replica, it, TAG_SAMPLE_ATT, (u64)g, 0);
@@ -665,6 +678,11 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
     es = block_fix(es, smf);
     inline_att = block_sum(inline_att, sm);
     death_hf = block_sum(death_hf, sm);
+    if (p.multispawn) {
+        __shared__ double smd[32];
+        cl_att = block_sum(cl_att, smd);
+        if (threadIdx.x == 0 && cl_att != 0.0) atomicAdd(&st->cl_att, cl_att);
+    }
     if (threadIdx.x == 0) {
         if (death_hf) atomicAdd((unsigned long long *)&wa.death[0], (unsigned long long)death_hf);
         wa.enum_part[2 * (enum_base + vb)] = es.lo;
@@ -683,6 +701,12 @@ template <int K, typename R>
 __device__ __forceinline__ void d_attempts(const SysDev &s, const ListView &L, DevStep *st, const RunParams &p,
                                                               const WorkArrays &wa, const SpawnBuf &sp, const ClusterBuf &cl)
 {
+    // the cluster attempts of a runaway population are not run (their
+    // packed count may have wrapped); the step reports the error instead
+    if ((st->err & ERRB_RUNAWAY) || st->cl_att > (double)p.work_cap) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(&st->err, (unsigned)ERRB_RUNAWAY);
+        return;
+    }
     const i64 n = st->n_occ, tf = st->fnc_attempts;
     i64 ncl = (i64)(st->cl_packed >> CL_SHIFT);
     if (ncl > cl.cap) ncl = cl.cap;

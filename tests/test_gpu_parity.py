@@ -7,6 +7,7 @@ different order) must agree to 1e-12 relative.
 """
 import os
 import tempfile
+import time
 
 import numpy as np
 import pytest
@@ -301,6 +302,41 @@ def test_list_overflow_is_reported(ccmc):
         ctx.step(30)
         ctx.sync()
     assert e.value.status == 7
+
+
+def test_runaway_population_is_reported(ccmc):
+    """A population far above the target (more samples in one step than
+    max(64 x target, 2^24)) abandons the step at once with CCMC_ERR_RUNAWAY."""
+    w = workload("ueg14_m38_ccsd", target_pop=100.0)
+    ctx = ccmc.from_workload(w)
+    hf = np.array([[(1 << 14) - 1]], dtype=np.uint64)
+    ctx.set_list(hf, np.array([((1 << 24) + 1000) * 65536], dtype=np.int64))
+    t = time.perf_counter()
+    with pytest.raises(ccmc.CCMCError) as e:
+        ctx.step(1)
+        ctx.sync()
+    assert e.value.status == 9
+    assert time.perf_counter() - t < 10.0
+
+
+def test_runaway_cluster_attempts_are_not_run(ccmc):
+    """Multi-spawn with a unit reference weight under 9e6 excitor particles:
+    every composite cluster carries ~1e7 or more attempts.  The attempts are
+    not run; the step ends quickly with CCMC_ERR_RUNAWAY."""
+    w = workload("ueg14_m114_ccsdt_fnc_ms", target_pop=100.0)
+    so = oracle.System.ueg(w["nel"], w["nso"], w["rs"], 2)
+    keys = so.space_keys(2, expand_top=False)            # reference + doubles, in key order
+    bits = np.stack([so.to_words(so.unrank(int(k))) for k in keys])
+    pops = np.full(len(keys), 5000 * 65536, dtype=np.int64)
+    pops[0] = 65536
+    ctx = ccmc.from_workload(w)
+    ctx.set_list(bits, pops)
+    t = time.perf_counter()
+    with pytest.raises(ccmc.CCMCError) as e:
+        ctx.step(1)
+        ctx.sync()
+    assert e.value.status == 9
+    assert time.perf_counter() - t < 10.0
 
 
 def test_rejects_bad_lists(ccmc):
