@@ -138,27 +138,51 @@ def algorithmic_bytes(phase: str, recs: list, nw: int) -> float:
 # CPU oracle (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
 
+STATE_ITER, STATE_SHIFT = 1500, -0.35   # iteration and shift of the synthetic full-size states
+
+
+def synthetic_state(w):
+    """The molecule workload's full-size start state: (words, pops, N_total)."""
+    from ccmc_inputs import molecule_state
+
+    words, pops, _ = molecule_state(norb=w["norb"], nocc=w["nel"] // 2, n_total=w["target_pop"],
+                                    seed=w.get("state_seed", 31))
+    return words, pops, float(abs(pops).sum()) / 65536.0
+
+
+def state_name(w):
+    return "oracle-made full-space state" if w["kind"] == "ueg" else "synthetic full-size molecule state"
+
+
 def oracle_state(w):
-    """The workload at its target size, made by the oracle: every excitor of
-    the truncated space occupied with seeded populations summing to the
-    target (the oracle enumerates the space with its excitation generator)."""
+    """The workload at its target size for the oracle: for the gas every
+    excitor of the truncated space occupied with seeded populations summing to
+    the target (the oracle enumerates the space with its excitation
+    generator); for the molecule the synthetic full-size state."""
     import numpy as np
 
     import oracle
-    from ccmc_inputs import synthetic_populations
+    from ccmc_inputs import molecule_integrals, synthetic_populations
 
-    so = oracle.System.ueg(w["nel"], w["nso"], w["rs"], w["lmax"])
-    keys = so.space_keys(w["lmax"], expand_top=False)
-    dets = [so.unrank(int(k)) for k in keys]
-    levels = [so.level(d) for d in dets]
-    bits = np.stack([so.to_words(d) for d in dets])
-    pops = synthetic_populations(levels, w["target_pop"], seed=21)
+    if w["kind"] == "ueg":
+        so = oracle.System.ueg(w["nel"], w["nso"], w["rs"], w["lmax"])
+        keys = so.space_keys(w["lmax"], expand_top=False)
+        dets = [so.unrank(int(k)) for k in keys]
+        levels = [so.level(d) for d in dets]
+        bits = np.stack([so.to_words(d) for d in dets])
+        pops = synthetic_populations(levels, w["target_pop"], seed=21)
+        ntot = w["target_pop"]
+    else:
+        h1, eri = molecule_integrals(norb=w["norb"], nocc=w["nel"] // 2, seed=w.get("molecule_seed", 7),
+                                     scale=w.get("eri_scale", 1.0))
+        so = oracle.System.generic(w["nel"], h1, eri, w["lmax"])
+        bits, pops, ntot = synthetic_state(w)
     sim = oracle.Sim(so, tau=w["tau"], target_pop=w["target_pop"], d0_init=w["d0_init"], shift_a=w["shift_a"],
                      zeta=w["zeta"], spawn_cutoff=w["spawn_cutoff"], fnc=w["fnc"], multispawn=w["multispawn"],
                      a_thresh=w["a_thresh"], seed=w["seed"])
     sim.set_list_words(bits, pops)
-    sim.set_state(1500, -0.35, True, w["target_pop"])
-    return sim, len(keys)
+    sim.set_state(STATE_ITER, STATE_SHIFT, True, ntot)
+    return sim, len(pops)
 
 
 def slices_for(sim, per_slice=200_000):
@@ -167,14 +191,14 @@ def slices_for(sim, per_slice=200_000):
     return max(1, (r0.n_sel + r0.n_visit + per_slice - 1) // per_slice)
 
 
-def oracle_slices(sim, n_occ, nslices, count, it0=1500):
+def oracle_slices(sim, n_occ, nslices, count, it0=STATE_ITER):
     """Times `count` slices, each 1/nslices of one full step's visits and
     cluster samples (propagation only).  Returns (samples, seconds, spawned)."""
     samples, secs, spawned = 0, 0.0, 0
     n_sel = None
     for k in range(count):
         q = k % nslices
-        sim.set_state(it0 + k // nslices, -0.35, True, 1.0)
+        sim.set_state(it0 + k // nslices, STATE_SHIFT, True, 1.0)
         if n_sel is None:
             r0 = sim.sample_range(0, 0, 0, 0)
             n_sel = r0.n_sel
@@ -202,12 +226,12 @@ def run_reference(args, w):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "keys_per_s": spawned / secs,
-        "config": {"workload": w["name"], "electrons": w["nel"], "spin_orbitals": w["nso"],
+        "config": {"workload": w["name"], "electrons": w["nel"], "spin_orbitals": w.get("nso", 2 * w.get("norb", 0)),
                    "truncation": w["lmax"], "target_pop": w["target_pop"], "tau": w["tau"],
                    "sampling": "fnc+multispawn" if w["fnc"] else "original"},
         "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} slices of 1/{nslices} of a full step (visits + cluster samples, "
-                                   f"propagation only) on the oracle-made full-space state, N_total = target"},
+                                   f"propagation only) on the {state_name(w)}, N_total = target"},
         "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -237,6 +261,15 @@ def run_gpu(args, w):
     ctx = ccmc.from_workload(w, replica=rank, stream=stream.cuda_stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
 
+    restore = None
+    if w.get("from_state"):
+        # every timed step starts from the same synthetic full-size state,
+        # restored (outside the timed region) before the step
+        words, pops0, ntot0 = synthetic_state(w)
+
+        def restore():
+            ctx.set_list(words, pops0)
+            ctx.set_state(STATE_ITER, STATE_SHIFT, 1, ntot0)
     # growth to the target population (untimed).  Large workloads grow at a
     # fraction f of the target, then every population (reference included)
     # is scaled by 1/f: t_HF exp(T/t_HF) scales as a whole, so this is the
@@ -247,7 +280,7 @@ def run_gpu(args, w):
     t_grow = time.perf_counter()
     grown = 0
     reached = None
-    while grown < args.grow_max:
+    while restore is None and grown < args.grow_max:
         gctx.step(w["shift_a"])
         grown += w["shift_a"]
         it, shift, vary, nprev = gctx.get_state()
@@ -261,6 +294,10 @@ def run_gpu(args, w):
             break
     gctx.sync()
     state_note = f"grown from HF for {grown} steps"
+    if restore is not None:
+        restore()
+        state_note = (f"synthetic full-size state ({len(pops0)} excitors of levels 0-4, N_total = {ntot0:.4g}), "
+                      f"restored before every timed step")
     if gctx is not ctx:
         bits, _, pop = gctx.get_list()
         it, shift, vary, nprev = gctx.get_state()
@@ -274,16 +311,26 @@ def run_gpu(args, w):
     ctx.records()
 
     def timed(nsteps):
+        """Times nsteps steps; returns (per-step ms, their records).  With a
+        restored start state each step's record is read before the next
+        restore (restoring rewinds the iteration count)."""
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
+        recs_ = []
         with torch.cuda.stream(stream):
             for k in range(nsteps):
+                if restore is not None:
+                    recs_ += ctx.records()
+                    restore()
                 flush.fill_(k)
                 starts[k].record(stream)
                 ctx.step(1)
                 ends[k].record(stream)
         stream.synchronize()
-        return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        recs_ += ctx.records()
+        if restore is not None:
+            recs_ = recs_[-nsteps:]
+        return [s.elapsed_time(e) for s, e in zip(starts, ends)], recs_
 
     timed(args.warmup)
     ctx.records()
@@ -295,14 +342,13 @@ def run_gpu(args, w):
     torch.cuda.synchronize()
     if args.profile_window:
         torch.cuda.profiler.start()
-    times = timed(args.steps)
+    times, recs = timed(args.steps)
     torch.cuda.synchronize()
     if args.profile_window:
         torch.cuda.profiler.stop()
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    recs = ctx.records()
     _, _, launches1 = ctx.phase_times()
     ms_total = sum(times)
     samples = sum(r["n_sel"] + r["n_visit"] for r in recs)
@@ -321,6 +367,8 @@ def run_gpu(args, w):
     ctx.profile(True)
     with torch.cuda.stream(stream):
         for k in range(args.profile_steps):
+            if restore is not None:
+                restore()
             flush.fill_(k)
             ctx.step(1)
     stream.synchronize()
@@ -336,6 +384,8 @@ def run_gpu(args, w):
 
     # end-to-end through the public API with host buffers: upload the excip
     # list, one step, download the list and the estimators
+    if restore is not None:
+        restore()
     bits, _, pop = ctx.get_list()
     e2e_steps = args.e2e_steps
     h2d = d2h = 0
@@ -344,15 +394,22 @@ def run_gpu(args, w):
     t0 = time.perf_counter()
     for k in range(e2e_steps):
         ctx.set_list(bits, pop)
+        if restore is not None:
+            ctx.set_state(STATE_ITER, STATE_SHIFT, 1, ntot0)
         h2d += bits.nbytes + pop.nbytes
         ctx.step(1)
-        bits, keys_h, pop = ctx.get_list()
+        out_bits, keys_h, out_pop = ctx.get_list()
         en = ctx.energy()
-        d2h += bits.nbytes + keys_h.nbytes + pop.nbytes + 40
+        d2h += out_bits.nbytes + keys_h.nbytes + out_pop.nbytes + 40
+        if restore is None:
+            bits, pop = out_bits, out_pop
     torch.cuda.synchronize()
     e2e_secs = time.perf_counter() - t0
     erecs = ctx.records()
-    e2e_samples = sum(r["n_sel"] + r["n_visit"] for r in erecs[-e2e_steps:])
+    if restore is not None:   # every e2e step ran from the same state
+        e2e_samples = e2e_steps * (erecs[-1]["n_sel"] + erecs[-1]["n_visit"])
+    else:
+        e2e_samples = sum(r["n_sel"] + r["n_visit"] for r in erecs[-e2e_steps:])
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -366,10 +423,10 @@ def run_gpu(args, w):
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32" if w.get("precision") == "fp32" else "f64", "data": "synthetic",
         "keys_per_s": keys_all / (ms_max * 1e-3),
-        "config": {"workload": w["name"], "electrons": w["nel"], "spin_orbitals": w["nso"], "truncation": w["lmax"],
-                   "target_pop": w["target_pop"], "tau": w["tau"],
+        "config": {"workload": w["name"], "electrons": w["nel"], "spin_orbitals": w.get("nso", 2 * w.get("norb", 0)),
+                   "truncation": w["lmax"], "target_pop": w["target_pop"], "tau": w["tau"],
                    "sampling": "fnc+multispawn" if w["fnc"] else "original",
                    "state": f"{state_note} ({t_grow:.1f} s), shift varying",
                    "n_occ": recs[-1]["nocc_after"], "n_total": recs[-1]["ntot_after"] / 65536.0,
@@ -571,13 +628,13 @@ def cpu_baseline(w):
     samples, secs, _ = oracle_slices(sim, n_occ, nslices, done)
     return {"value": samples / secs, "unit": "samples/s", "cores": 1, "kind": "oracle",
             "sample": f"{done} slice(s) of 1/{nslices} of a full step (visits + cluster samples, propagation only) "
-                      f"on the oracle-made full-space state at N_total = target, {secs:.1f} s"}
+                      f"on the {state_name(w)} at N_total = target, {secs:.1f} s"}
 
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ueg14_m114_ccsdt_fnc_ms")

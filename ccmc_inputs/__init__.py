@@ -32,9 +32,12 @@ WORKLOADS = {
     # UEG 14 e / 114 spin-orbitals (57 plane waves), CCSDT, full non-composite + multi-spawn
     "ueg14_m114_ccsdt_fnc_ms": dict(kind="ueg", nel=14, nso=114, rs=1.0, lmax=3, target_pop=1.0e6,
                                     tau=0.005, nsteps=2000, seed=1, fnc=True, multispawn=True),
-    # synthetic molecule: 20 e in 41 spatial orbitals (82 spin-orbitals), CCSDTQ
+    # synthetic molecule: 20 e in 41 spatial orbitals (82 spin-orbitals), CCSDTQ.
+    # With these integrals no population grown from the reference settles
+    # (every run tried ran away within 600 steps), so each timed step starts
+    # from the same synthetic full-size state (molecule_state).
     "mol20_m82_ccsdtq": dict(kind="generic", nel=20, norb=41, lmax=4, target_pop=1.0e7,
-                             tau=0.005, nsteps=50, seed=1, molecule_seed=7, grow_fraction=0.1),
+                             tau=0.005, nsteps=50, seed=1, molecule_seed=7, from_state=True, state_seed=31),
     # UEG 54 e / 162 spin-orbitals (81 plane waves), CCSD, FP32 matrix elements.
     # 10^4 initial particles on HF: from 100 the original sampler stays below
     # the shoulder on this system and the population blows up.  Grown at 1% of
@@ -142,3 +145,72 @@ def synthetic_populations(levels, n_total: float, seed: int, ref_fraction: float
     pops = pops * signs
     pops[0] = int(round(ref_fraction * n_total * 65536.0))
     return pops
+
+
+def random_excitors(norb: int, nocc: int, level: int, count: int, rng) -> np.ndarray:
+    """count determinants drawn uniformly from the S_z-conserving level-`level`
+    excitations of the closed-shell reference (nocc doubly occupied spatial
+    orbitals out of norb; spin-orbital 2p is alpha, 2p+1 beta), as
+    [count, ceil(2 norb / 64)] uint64 words (bit q of word q // 64).  Repeats
+    are possible."""
+    nvir = norb - nocc
+    nw = (2 * norb + 63) // 64
+    # number of alpha holes a: weight C(nocc,a) C(nocc,L-a) C(nvir,a) C(nvir,L-a)
+    from math import comb
+
+    wts = np.array([comb(nocc, a) * comb(nocc, level - a) * comb(nvir, a) * comb(nvir, level - a)
+                    for a in range(level + 1)], dtype=np.float64)
+    na = rng.choice(level + 1, size=count, p=wts / wts.sum())
+    words = np.zeros((count, nw), dtype=np.uint64)
+    hf = np.zeros(nw, dtype=np.uint64)
+    for q in range(2 * nocc):
+        hf[q // 64] |= np.uint64(1) << np.uint64(q % 64)
+    words[:] = hf
+    for a in range(level + 1):
+        rows = np.nonzero(na == a)[0]
+        if len(rows) == 0:
+            continue
+        picks = []
+        for spin, k in ((0, a), (1, level - a)):
+            if k == 0:
+                continue
+            holes = np.argsort(rng.random((len(rows), nocc)), axis=1)[:, :k]
+            parts = nocc + np.argsort(rng.random((len(rows), nvir)), axis=1)[:, :k]
+            picks += [2 * holes + spin, 2 * parts + spin]
+        if not picks:
+            continue
+        idx = np.concatenate(picks, axis=1).astype(np.uint64)   # flipped spin-orbitals (all distinct)
+        for w in range(nw):
+            inw = (idx // np.uint64(64)) == np.uint64(w)
+            bit = np.where(inw, np.left_shift(np.uint64(1), idx % np.uint64(64)), np.uint64(0))
+            words[rows, w] ^= np.bitwise_or.reduce(bit, axis=1)
+    return words
+
+
+def molecule_state(norb: int = 41, nocc: int = 10, draws=None, n_total: float = 1.0e7, seed: int = 31,
+                   ref_fraction: float = 0.3):
+    """A full-size synthetic CCSDTQ list for the molecule-like Hamiltonian:
+    the reference plus distinct excitors drawn uniformly per level (draws =
+    {level: count}, repeats removed), in canonical order (unsigned bit-string
+    order, most significant word first), with synthetic_populations weights.
+    Returns (words [n, nw] uint64, pops int64, levels)."""
+    if draws is None:
+        draws = {1: 4000, 2: 400_000, 3: 1_500_000, 4: 2_500_000}
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = [random_excitors(norb, nocc, lv, c, rng) for lv, c in sorted(draws.items())]
+    hf = random_excitors(norb, nocc, 0, 1, rng)
+    words = np.concatenate([hf] + parts, axis=0)
+    order = np.lexsort(tuple(words[:, w] for w in range(words.shape[1])))   # last word is the primary key
+    words = words[order]
+    keep = np.ones(len(words), dtype=bool)
+    keep[1:] = np.any(words[1:] != words[:-1], axis=1)
+    words = words[keep]
+    hfw = hf[0]
+    flips = np.zeros(len(words), dtype=np.int64)
+    for w in range(words.shape[1]):
+        x = np.ascontiguousarray(words[:, w] ^ hfw[w])
+        flips += np.unpackbits(x.view(np.uint8).reshape(-1, 8), axis=1).sum(axis=1).astype(np.int64)
+    levels = flips // 2
+    assert np.array_equal(words[0], hfw) and levels[0] == 0
+    pops = synthetic_populations(levels, n_total, seed, ref_fraction)
+    return words, pops, levels

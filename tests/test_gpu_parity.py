@@ -164,6 +164,31 @@ def test_ueg114_full_size_step_bitexact(ccmc):
         _same_list(sim, ctx)
 
 
+def test_molecule_full_size_step_bitexact(ccmc):
+    """The synthetic molecule (20 electrons, 82 spin-orbitals, CCSDTQ, two-word
+    determinants) at full size: about 4e6 occupied excitors of levels 0-4 and
+    N_total of about 1.2e7, one step in the production launch configuration.
+    Spawned records, death deltas, the merged list and the record must match."""
+    from ccmc_inputs import molecule_state
+
+    w = workload("mol20_m82_ccsdtq")
+    h1, eri = molecule_integrals(norb=41, nocc=10, seed=7)
+    w.update(h1=h1, eri=eri, nso=82)
+    so, sim, ctx = _pair(ccmc, w)
+    words, pops, _ = molecule_state()
+    ntot = float(np.abs(pops).sum()) / 65536.0
+    sim.set_list_words(words, pops)
+    ctx.set_list(words, pops)
+    sim.set_state(1500, -0.35, True, ntot)
+    ctx.set_state(1500, -0.35, True, ntot)
+    rec = sim.step()
+    ctx.step(1)
+    _same_record(rec, ctx.records()[-1])
+    assert rec.n_sel > 10_000_000 and rec.n_spawned > 1_000_000
+    _same_spawned(sim, ctx)
+    _same_list(sim, ctx)
+
+
 def test_molecule_all_samplers_bitexact(ccmc):
     """A small molecule-like Hamiltonian (singles exist, so composite clusters
     collapse onto the truncated space and composite death is exercised)."""
