@@ -525,8 +525,12 @@ def run_gpu_batched(args):
         clocks = ClockSampler(local)
         clocks.start()
         torch.cuda.synchronize()
+        if args.profile_window:
+            torch.cuda.profiler.start()
         ms_batched = timed(lambda: batch.step(1), stream, args.steps)
         torch.cuda.synchronize()
+        if args.profile_window:
+            torch.cuda.profiler.stop()
         clk = clocks.stop()
         _, _, launches1 = batch.phase_times()
         recs = [c.records() for c in ctxs]

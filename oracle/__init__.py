@@ -101,6 +101,7 @@ def lib():
             "orc_hij_f": (c_double, [c_void_p, u64p, u64p]),
             "orc_system_set_fp32": (c_int, [c_void_p]),
             "orc_hdiag_rel": (c_double, [c_void_p, u64p]),
+            "orc_hdiag_rel_f": (c_double, [c_void_p, u64p]),
             "orc_excitor_sign": (c_int, [c_void_p, u64p]),
             "orc_level": (c_int, [c_void_p, u64p]),
             "orc_collapse": (c_int, [c_void_p, c_int, u64p, u64p, i32p]),
@@ -252,8 +253,14 @@ class System:
         return self
 
     def hdiag_rel(self, d: int) -> float:
+        """H_DD - E_HF in the excitation form the step uses."""
         w, wp = _u64(self.to_words(d))
         return lib().orc_hdiag_rel(self._h, wp)
+
+    def hdiag_rel_f(self, d: int) -> float:
+        """The same in single precision (FP32 form; the system must be set_fp32)."""
+        w, wp = _u64(self.to_words(d))
+        return lib().orc_hdiag_rel_f(self._h, wp)
 
     def excitor_sign(self, d: int) -> int:
         w, wp = _u64(self.to_words(d))

@@ -154,6 +154,7 @@ typedef struct {
     double ecore;
     /* common */
     double ehf_rel;      /* <HF|H|HF> without the constant ecore */
+    double *fock;        /* F_p = h_pp + sum_{k in HF, k != p} <pk||pk>, per spin-orbital */
     uint64_t binom[200][8];
     uint64_t cocc;       /* number of hole sets with <= l holes */
     uint64_t nvranks;    /* number of particle sets with <= l particles */
@@ -167,6 +168,7 @@ typedef struct {
      * precision from tables rounded from the FP64 ones */
     int fp32;
     float *tkin_f, *vtab_f, *h1_f, *eri_f;
+    float *fock_f;       /* F rounded to single precision */
     float ehf_rel_f;
     float inv_pgen_ueg_f, inv_pgen_single_f[2], inv_pgen_double_f[3];
 } orc_system;
@@ -191,9 +193,10 @@ static uint64_t count_upto(const orc_system *s, int n, int kmax)
     return c;
 }
 
-static double h_diag_rel(const orc_system *s, const det_t *d);
+static double h_diag_abs(const orc_system *s, const det_t *d);
+static int fock_setup(orc_system *s);
 
-static void common_setup(orc_system *s)
+static int common_setup(orc_system *s)
 {
     fill_binom(s);
     s->nw = (s->nso + 63) / 64;
@@ -203,8 +206,8 @@ static void common_setup(orc_system *s)
     s->nvranks = count_upto(s, s->nso - s->nel, s->lmax);
     s->npairs = (uint64_t)s->nel * (uint64_t)(s->nel - 1) / 2;
     s->nvirt = (uint64_t)(s->nso - s->nel);
-    s->ehf_rel = 0.0;
-    s->ehf_rel = h_diag_rel(s, &s->hf);
+    s->ehf_rel = h_diag_abs(s, &s->hf);
+    return fock_setup(s);
 }
 
 static int cmp_kvec(const void *a, const void *b)
@@ -223,6 +226,7 @@ void orc_system_free(orc_system *s)
     free(s->kv); free(s->grid); free(s->tkin); free(s->vtab);
     free(s->h1); free(s->eri);
     free(s->tkin_f); free(s->vtab_f); free(s->h1_f); free(s->eri_f);
+    free(s->fock); free(s->fock_f);
     free(s);
 }
 
@@ -282,7 +286,7 @@ orc_system *orc_ueg_new(int nel, int nso, double rs, int lmax)
     s->vtab = (double *)malloc(sizeof(double) * (size_t)s->n2tab);
     s->vtab[0] = 0.0;
     for (int n2 = 1; n2 < s->n2tab; n2++) s->vtab[n2] = 1.0 / ((ORC_PI * s->L) * (double)n2);
-    common_setup(s);
+    if (common_setup(s)) { orc_system_free(s); return NULL; }
     s->inv_pgen_ueg = (double)(s->npairs * s->nvirt) * 0.5;
     return s;
 }
@@ -302,7 +306,7 @@ orc_system *orc_generic_new(int nel, int norb, const double *h1, const double *e
     if (!s->h1 || !s->eri) { orc_system_free(s); return NULL; }
     memcpy(s->h1, h1, sizeof(double) * n2);
     memcpy(s->eri, eri, sizeof(double) * n4);
-    common_setup(s);
+    if (common_setup(s)) { orc_system_free(s); return NULL; }
     /* spin-resolved occupied / virtual counts of the reference */
     s->no[0] = s->no[1] = 0;
     for (int p = 0; p < nel; p++) s->no[spin_of(p)]++;
@@ -381,10 +385,67 @@ static double h_diag_abs(const orc_system *s, const det_t *d)
     return e1 + e2;
 }
 
-/* H_DD - E_HF (both without the core constant). */
+/* <pq||pq> = <pq|pq> - <pq|qp> for p != q.  Gas: the direct term is the
+ * omitted q = 0 Coulomb term, so only the exchange of equal spins remains
+ * (callers skip pairs of opposite spin there).  Molecule: (pp|qq) minus
+ * (pq|qp) for equal spins. */
+static double pair_ex(const orc_system *s, int p, int q)
+{
+    if (s->kind == 0) return -s->vtab[ueg_n2_between(s, p, q)];
+    int P = spat_of(p), Q = spat_of(q);
+    double t = eri_at(s, P, P, Q, Q);
+    if (spin_of(p) == spin_of(q)) t = t - eri_at(s, P, Q, Q, P);
+    return t;
+}
+
+static int pair_zero(const orc_system *s, int p, int q)
+{
+    return s->kind == 0 && spin_of(p) != spin_of(q);
+}
+
+/* Fock diagonal of the reference, per spin-orbital: one-body term, then
+ * <pk||pk> over the occupied k != p ascending. */
+static int fock_setup(orc_system *s)
+{
+    s->fock = (double *)malloc(sizeof(double) * (size_t)s->nso);
+    if (!s->fock) return ORC_ERR_OOM;
+    for (int p = 0; p < s->nso; p++) {
+        double f = s->kind == 0 ? s->tkin[p] : s->h1[spat_of(p) * s->norb + spat_of(p)];
+        for (int k = 0; k < s->nel; k++) {
+            if (k == p || pair_zero(s, p, k)) continue;
+            f = f + pair_ex(s, p, k);
+        }
+        s->fock[p] = f;
+    }
+    return 0;
+}
+
+/* H_DD - E_HF from the excitation of D relative to HF (holes H, particles P,
+ * both ascending): sum_P F_a - sum_H F_i + sum_{i<j in H} <ij||ij>
+ * + sum_{a<b in P} <ab||ab> - sum_{a in P, i in H} <ai||ai>, in this order.
+ * It equals the difference of the two Slater-Condon diagonals (both without
+ * the core constant). */
 static double h_diag_rel(const orc_system *s, const det_t *d)
 {
-    return h_diag_abs(s, d) - s->ehf_rel;
+    int hol[64 * OW], par[64 * OW], nh = 0, np = 0;
+    for (int p = 0; p < s->nso; p++) {
+        int b = det_bit(d, p), r = det_bit(&s->hf, p);
+        if (r && !b) hol[nh++] = p;
+        if (b && !r) par[np++] = p;
+    }
+    double e = 0.0;
+    for (int x = 0; x < np; x++) e = e + s->fock[par[x]];
+    for (int x = 0; x < nh; x++) e = e - s->fock[hol[x]];
+    for (int x = 0; x < nh; x++)
+        for (int y = x + 1; y < nh; y++)
+            if (!pair_zero(s, hol[x], hol[y])) e = e + pair_ex(s, hol[x], hol[y]);
+    for (int x = 0; x < np; x++)
+        for (int y = x + 1; y < np; y++)
+            if (!pair_zero(s, par[x], par[y])) e = e + pair_ex(s, par[x], par[y]);
+    for (int x = 0; x < np; x++)
+        for (int y = 0; y < nh; y++)
+            if (!pair_zero(s, par[x], hol[y])) e = e - pair_ex(s, par[x], hol[y]);
+    return e;
 }
 
 /* <bra|H|ket> for canonical determinants.  The phase gamma is that of
@@ -479,9 +540,38 @@ static float h_diag_abs_f(const orc_system *s, const det_t *d)
     return e1 + e2;
 }
 
+static float pair_ex_f(const orc_system *s, int p, int q)
+{
+    if (s->kind == 0) return -s->vtab_f[ueg_n2_between(s, p, q)];
+    int P = spat_of(p), Q = spat_of(q);
+    float t = eri_f_at(s, P, P, Q, Q);
+    if (spin_of(p) == spin_of(q)) t = t - eri_f_at(s, P, Q, Q, P);
+    return t;
+}
+
+/* The excitation form of H_DD - E_HF in single precision: Fock diagonal
+ * rounded from FP64, pair terms from the rounded tables, same order. */
 static float h_diag_rel_f(const orc_system *s, const det_t *d)
 {
-    return h_diag_abs_f(s, d) - s->ehf_rel_f;
+    int hol[64 * OW], par[64 * OW], nh = 0, np = 0;
+    for (int p = 0; p < s->nso; p++) {
+        int b = det_bit(d, p), r = det_bit(&s->hf, p);
+        if (r && !b) hol[nh++] = p;
+        if (b && !r) par[np++] = p;
+    }
+    float e = 0.0f;
+    for (int x = 0; x < np; x++) e = e + s->fock_f[par[x]];
+    for (int x = 0; x < nh; x++) e = e - s->fock_f[hol[x]];
+    for (int x = 0; x < nh; x++)
+        for (int y = x + 1; y < nh; y++)
+            if (!pair_zero(s, hol[x], hol[y])) e = e + pair_ex_f(s, hol[x], hol[y]);
+    for (int x = 0; x < np; x++)
+        for (int y = x + 1; y < np; y++)
+            if (!pair_zero(s, par[x], par[y])) e = e + pair_ex_f(s, par[x], par[y]);
+    for (int x = 0; x < np; x++)
+        for (int y = 0; y < nh; y++)
+            if (!pair_zero(s, par[x], hol[y])) e = e - pair_ex_f(s, par[x], hol[y]);
+    return e;
 }
 
 /* <bra|H|ket> in single precision for bra != ket (0 for the diagonal). */
@@ -538,8 +628,10 @@ int orc_system_set_fp32(orc_system *s)
         for (int g = 0; g < 2; g++) s->inv_pgen_single_f[g] = (float)s->inv_pgen_single[g];
         for (int c = 0; c < 3; c++) s->inv_pgen_double_f[c] = (float)s->inv_pgen_double[c];
     }
+    s->fock_f = (float *)malloc(sizeof(float) * (size_t)s->nso);
+    if (!s->fock_f) return ORC_ERR_OOM;
+    for (int p = 0; p < s->nso; p++) s->fock_f[p] = (float)s->fock[p];
     s->fp32 = 1;
-    s->ehf_rel_f = 0.0f;
     s->ehf_rel_f = h_diag_abs_f(s, &s->hf);
     return 0;
 }
@@ -1265,6 +1357,12 @@ double orc_hdiag_rel(const orc_system *s, const uint64_t *w)
 {
     det_t d = load_det(s, w);
     return h_diag_rel(s, &d);
+}
+
+double orc_hdiag_rel_f(const orc_system *s, const uint64_t *w)
+{
+    det_t d = load_det(s, w);
+    return s->fp32 ? (double)h_diag_rel_f(s, &d) : 0.0;
 }
 
 int orc_excitor_sign(const orc_system *s, const uint64_t *w)

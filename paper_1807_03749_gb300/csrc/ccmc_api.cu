@@ -38,9 +38,9 @@ struct HostSys {
     u64 npairs = 0, nvirt = 0, ns = 0, nd = 0, ndcase[3] = {0, 0, 0};
     int no[2] = {0, 0}, nv[2] = {0, 0};
     double inv_pgen_ueg = 0.0, inv_pgen_single[2] = {0, 0}, inv_pgen_double[3] = {0, 0, 0};
+    std::vector<double> fock;     // reference Fock diagonal per spin-orbital
     // FP32 form
-    std::vector<float> tkin_f, vtab_f, h1_f, eri_f;
-    float ehf_rel_f = 0.0f;
+    std::vector<float> tkin_f, vtab_f, h1_f, eri_f, fock_f;
 };
 
 void fill_binom(HostSys &h)
@@ -82,36 +82,34 @@ double host_diag(const HostSys &h, const std::vector<int> &occ)
     return e1 + e2;
 }
 
-// the same in single precision on the rounded tables (FP32 form)
-float host_diag_f(const HostSys &h, const std::vector<int> &occ)
+// <pq||pq> for p != q (same definition and operation order as the device)
+double host_pair_ex(const HostSys &h, int p, int q)
 {
-    const int n = (int)occ.size();
     if (h.kind == CCMC_UEG) {
-        float tsum = 0.0f, xsum = 0.0f;
-        for (int i = 0; i < n; i++) tsum = tsum + h.tkin_f[occ[i]];
-        for (int i = 0; i < n; i++)
-            for (int j = i + 1; j < n; j++)
-                if (((occ[i] ^ occ[j]) & 1) == 0) {
-                    const int *a = &h.kv[3 * (occ[i] >> 1)], *b = &h.kv[3 * (occ[j] >> 1)];
-                    int dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
-                    xsum = xsum + h.vtab_f[dx * dx + dy * dy + dz * dz];
-                }
-        return tsum - xsum;
+        const int *a = &h.kv[3 * (p >> 1)], *b = &h.kv[3 * (q >> 1)];
+        int dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+        return -h.vtab[dx * dx + dy * dy + dz * dz];
     }
-    float e1 = 0.0f, e2 = 0.0f;
+    const size_t no = (size_t)h.norb, P = p >> 1, Q = q >> 1;
+    double t = h.eri[((P * no + P) * no + Q) * no + Q];
+    if (((p ^ q) & 1) == 0) t = t - h.eri[((P * no + Q) * no + Q) * no + P];
+    return t;
+}
+
+// F_p = one-body term + <pk||pk> over the reference's occupied k != p ascending
+void host_fock(HostSys &h)
+{
+    h.fock.assign(h.nso, 0.0);
     const size_t no = (size_t)h.norb;
-    for (int i = 0; i < n; i++) {
-        int P = occ[i] >> 1;
-        e1 = e1 + h.h1_f[P * no + P];
-    }
-    for (int i = 0; i < n; i++)
-        for (int j = i + 1; j < n; j++) {
-            size_t P = occ[i] >> 1, Q = occ[j] >> 1;
-            float t = h.eri_f[((P * no + P) * no + Q) * no + Q];
-            if (((occ[i] ^ occ[j]) & 1) == 0) t = t - h.eri_f[((P * no + Q) * no + Q) * no + P];
-            e2 = e2 + t;
+    for (int p = 0; p < h.nso; p++) {
+        double f = h.kind == CCMC_UEG ? h.tkin[p] : h.h1[(size_t)(p >> 1) * no + (size_t)(p >> 1)];
+        for (int k = 0; k < h.nel; k++) {
+            if (k == p || (h.kind == CCMC_UEG && ((p ^ k) & 1))) continue;
+            f = f + host_pair_ex(h, p, k);
         }
-    return e1 + e2;
+        h.fock[p] = f;
+    }
+    h.fock_f.assign(h.fock.begin(), h.fock.end());
 }
 
 bool build_ueg(HostSys &h)
@@ -347,12 +345,12 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     std::vector<int> hfocc(nel);
     for (int p = 0; p < nel; p++) hfocc[p] = p;
     h.ehf_rel = host_diag(h, hfocc);
+    host_fock(h);
     // FP32 tables: rounded from the FP64 ones
     h.tkin_f.assign(h.tkin.begin(), h.tkin.end());
     h.vtab_f.assign(h.vtab.begin(), h.vtab.end());
     h.h1_f.assign(h.h1.begin(), h.h1.end());
     h.eri_f.assign(h.eri.begin(), h.eri.end());
-    h.ehf_rel_f = host_diag_f(h, hfocc);
     h.npairs = (u64)nel * (u64)(nel - 1) / 2;
     h.nvirt = (u64)(nso - nel);
     if (h.kind == CCMC_UEG) {
@@ -451,12 +449,12 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
         s.h1_f = (const float *)upload(h.h1_f.data(), h.h1_f.size() * sizeof(float));
         s.eri_f = (const float *)upload(h.eri_f.data(), h.eri_f.size() * sizeof(float));
     }
-    s.ehf_rel_f = h.ehf_rel_f;
+    s.fock = (const double *)upload(h.fock.data(), h.fock.size() * sizeof(double));
+    s.fock_f = (const float *)upload(h.fock_f.data(), h.fock_f.size() * sizeof(float));
     s.inv_pgen_ueg_f = (float)h.inv_pgen_ueg;
     for (int g = 0; g < 2; g++) s.inv_pgen_single_f[g] = (float)h.inv_pgen_single[g];
     for (int c = 0; c < 3; c++) s.inv_pgen_double_f[c] = (float)h.inv_pgen_double[c];
     s.cocc = h.cocc;
-    s.ehf_rel = h.ehf_rel;
 
     RunParams &rp = ctx->sc.prm;
     rp.tau = params->tau;

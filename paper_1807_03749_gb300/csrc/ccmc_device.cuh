@@ -68,10 +68,10 @@ struct SysDev {
     // rank key: tab[c * RANK_STRIDE + q] = sum_{j=0}^{l-c} C(q, j)
     const u64 *rank_tab;
     u64 cocc;
-    double ehf_rel;      // <HF|H|HF> without the core constant
+    const double *fock;  // reference Fock diagonal per spin-orbital
     // FP32 form: tables rounded from the FP64 ones
     const float *tkin_f, *vtab_f, *h1_f, *eri_f;
-    float ehf_rel_f;
+    const float *fock_f;
     float inv_pgen_ueg_f;
     float inv_pgen_single_f[2];
     float inv_pgen_double_f[3];
@@ -84,14 +84,14 @@ template <> struct Tab<double> {
     static __device__ __forceinline__ const double *vtab(const SysDev &s) { return s.vtab; }
     static __device__ __forceinline__ const double *h1(const SysDev &s) { return s.h1; }
     static __device__ __forceinline__ const double *eri(const SysDev &s) { return s.eri; }
-    static __device__ __forceinline__ double ehf(const SysDev &s) { return s.ehf_rel; }
+    static __device__ __forceinline__ const double *fock(const SysDev &s) { return s.fock; }
 };
 template <> struct Tab<float> {
     static __device__ __forceinline__ const float *tkin(const SysDev &s) { return s.tkin_f; }
     static __device__ __forceinline__ const float *vtab(const SysDev &s) { return s.vtab_f; }
     static __device__ __forceinline__ const float *h1(const SysDev &s) { return s.h1_f; }
     static __device__ __forceinline__ const float *eri(const SysDev &s) { return s.eri_f; }
-    static __device__ __forceinline__ float ehf(const SysDev &s) { return s.ehf_rel_f; }
+    static __device__ __forceinline__ const float *fock(const SysDev &s) { return s.fock_f; }
 };
 
 template <int K>
@@ -399,52 +399,60 @@ __device__ __forceinline__ R g2(const SysDev &s, int p, int q, int r, int t)
     return eri_at<R>(s, p >> 1, r >> 1, q >> 1, t >> 1);
 }
 
-// <D|H|D> without the core constant: one-body sum over occupied p ascending,
-// then the pair sum over p < q ascending (UEG: Tsum - Xsum; generic: e1 + e2),
-// in the arithmetic of R (double, or float for the FP32 form).
-template <int K, typename R>
-__device__ R diag_abs(const SysDev &s, const Det<K> &d)
+// <pq||pq> for p != q in the precision R: gas, minus the exchange Coulomb
+// term (callers skip opposite spins, whose pair term is the omitted q = 0
+// Coulomb term); molecule, (pp|qq) minus (pq|qp) for equal spins.
+template <typename R>
+__device__ __forceinline__ R pair_ex(const SysDev &s, int p, int q)
 {
-    int occ[64 * MAXK];
-    int n = 0;
-#pragma unroll
-    for (int w = 0; w < K; w++) {
-        u64 m = d.w[w];
-        while (m) {
-            occ[n++] = 64 * w + (__ffsll((long long)m) - 1);
-            m &= m - 1;
-        }
-    }
-    if (s.kind == 0) {
-        const R *tk = Tab<R>::tkin(s), *vt = Tab<R>::vtab(s);
-        R tsum = R(0), xsum = R(0);
-        for (int i = 0; i < n; i++) tsum = tsum + __ldg(&tk[occ[i]]);
-        for (int i = 0; i < n; i++)
-            for (int j = i + 1; j < n; j++)
-                if (((occ[i] ^ occ[j]) & 1) == 0) xsum = xsum + __ldg(&vt[ueg_n2(s, occ[i], occ[j])]);
-        return tsum - xsum;
-    }
-    const R *h1 = Tab<R>::h1(s);
-    R e1 = R(0), e2 = R(0);
-    for (int i = 0; i < n; i++) {
-        int P = occ[i] >> 1;
-        e1 = e1 + __ldg(&h1[P * s.norb + P]);
-    }
-    for (int i = 0; i < n; i++)
-        for (int j = i + 1; j < n; j++) {
-            int P = occ[i] >> 1, Q = occ[j] >> 1;
-            R t = eri_at<R>(s, P, P, Q, Q);
-            if (((occ[i] ^ occ[j]) & 1) == 0) t = t - eri_at<R>(s, P, Q, Q, P);
-            e2 = e2 + t;
-        }
-    return e1 + e2;
+    if (s.kind == 0) return -__ldg(&Tab<R>::vtab(s)[ueg_n2(s, p, q)]);
+    const int P = p >> 1, Q = q >> 1;
+    R t = eri_at<R>(s, P, P, Q, Q);
+    if (((p ^ q) & 1) == 0) t = t - eri_at<R>(s, P, Q, Q, P);
+    return t;
 }
 
-// H_DD - E_HF, promoted to double
+__device__ __forceinline__ bool pair_zero(const SysDev &s, int p, int q)
+{
+    return s.kind == 0 && ((p ^ q) & 1);
+}
+
+// H_DD - E_HF from the excitation of D relative to HF: holes H and particles
+// P ascending, sum_P F_a - sum_H F_i + sum_{i<j in H} <ij||ij>
+// + sum_{a<b in P} <ab||ab> - sum_{a in P, i in H} <ai||ai>, in this order,
+// in the precision R and promoted to double.  D is within the truncation
+// (at most 8 holes are read).
 template <int K, typename R>
 __device__ __forceinline__ double diag_rel(const SysDev &s, const Det<K> &d)
 {
-    return (double)(diag_abs<K, R>(s, d) - Tab<R>::ehf(s));
+    int hol[8], par[8], nh = 0, np = 0;
+#pragma unroll
+    for (int w = 0; w < K; w++) {
+        u64 hm = s.hf[w] & ~d.w[w];
+        u64 pm = d.w[w] & ~s.hf[w];
+        while (hm) {
+            if (nh < 8) hol[nh++] = 64 * w + (__ffsll((long long)hm) - 1);
+            hm &= hm - 1;
+        }
+        while (pm) {
+            if (np < 8) par[np++] = 64 * w + (__ffsll((long long)pm) - 1);
+            pm &= pm - 1;
+        }
+    }
+    const R *f = Tab<R>::fock(s);
+    R e = R(0);
+    for (int x = 0; x < np; x++) e = e + __ldg(&f[par[x]]);
+    for (int x = 0; x < nh; x++) e = e - __ldg(&f[hol[x]]);
+    for (int x = 0; x < nh; x++)
+        for (int y = x + 1; y < nh; y++)
+            if (!pair_zero(s, hol[x], hol[y])) e = e + pair_ex<R>(s, hol[x], hol[y]);
+    for (int x = 0; x < np; x++)
+        for (int y = x + 1; y < np; y++)
+            if (!pair_zero(s, par[x], par[y])) e = e + pair_ex<R>(s, par[x], par[y]);
+    for (int x = 0; x < np; x++)
+        for (int y = 0; y < nh; y++)
+            if (!pair_zero(s, par[x], hol[y])) e = e - pair_ex<R>(s, par[x], hol[y]);
+    return (double)e;
 }
 
 // <bra|H|ket> for determinants differing by one or two spin-orbitals.
@@ -537,12 +545,25 @@ __device__ __forceinline__ void pair_of(u64 idx, int &x, int &y)
     x = (int)(idx - (u64)yy * (yy - 1) / 2);
 }
 
+// 1/p_gen of a generator case (0: gas double; 1, 2: molecule single of spin
+// 0, 1; 3, 4, 5: molecule double of spin case 0, 1, mixed) in the precision
+// R, promoted to double.
+template <typename R>
+__device__ __forceinline__ double inv_pgen_of(const SysDev &s, int gc)
+{
+    if (sizeof(R) == 4) {
+        float f = gc == 0 ? s.inv_pgen_ueg_f : (gc < 3 ? s.inv_pgen_single_f[gc - 1] : s.inv_pgen_double_f[gc - 3]);
+        return (double)f;
+    }
+    return gc == 0 ? s.inv_pgen_ueg : (gc < 3 ? s.inv_pgen_single[gc - 1] : s.inv_pgen_double[gc - 3]);
+}
+
 // One draw of the excitation generator from dj.  Returns false for a null
 // draw; otherwise di, the holes (i<j) and particles (a<b) relative to dj, the
-// number of holes nh and 1/p_gen.
+// number of holes nh and the generator case gc (see inv_pgen_of).
 template <int K>
 __device__ bool excite(const SysDev &s, const Det<K> &dj, const R4 &r, Det<K> &di, int &nh, int &i, int &j,
-                       int &a, int &b, double &inv_pgen, float &inv_pgen_f)
+                       int &a, int &b, int &gc)
 {
     if (s.kind == 0) {
         int x, y;
@@ -566,8 +587,7 @@ __device__ bool excite(const SysDev &s, const Det<K> &dj, const R4 &r, Det<K> &d
         a = aa < bb ? aa : bb;
         b = aa < bb ? bb : aa;
         nh = 2;
-        inv_pgen = s.inv_pgen_ueg;
-        inv_pgen_f = s.inv_pgen_ueg_f;
+        gc = 0;
     } else if (below(r.v[0], s.ns_nd) < s.ns) {
         i = kth_occupied(dj, (int)below(r.v[1], (u64)s.nel));
         int sg = i & 1;
@@ -576,8 +596,7 @@ __device__ bool excite(const SysDev &s, const Det<K> &dj, const R4 &r, Det<K> &d
         if (a < 0) return false;
         j = b = 0;
         nh = 1;
-        inv_pgen = s.inv_pgen_single[sg];
-        inv_pgen_f = s.inv_pgen_single_f[sg];
+        gc = 1 + sg;
     } else {
         int x, y;
         pair_of(below(r.v[1], s.npairs), x, y);
@@ -603,8 +622,7 @@ __device__ bool excite(const SysDev &s, const Det<K> &dj, const R4 &r, Det<K> &d
         a = aa < bb ? aa : bb;
         b = aa < bb ? bb : aa;
         nh = 2;
-        inv_pgen = s.inv_pgen_double[c];
-        inv_pgen_f = s.inv_pgen_double_f[c];
+        gc = 3 + c;
     }
     di = dj;
     flip(di, i);

@@ -325,23 +325,40 @@ __device__ __forceinline__ i64 lower_bound_key(const u64 *keys, i64 n, u64 k)
 
 // One spawning attempt from dj carrying coefficient c_att (Sec. II):
 // value -dtau H_ij c_att s_D(i) / p_gen, stochastically rounded.
-template <int K, typename R>
-__device__ __forceinline__ bool spawn_attempt(const SysDev &s, const RunParams &p, const Det<K> &dj, double c_att,
-                                              const R4 &r, u64 &key, i64 &val, unsigned &err)
+// A spawning attempt in two halves.  attempt_draw runs the excitation
+// generator and the truncation check (about nine draws in ten end here for
+// the gas); attempt_finish computes the matrix element, the value, its
+// stochastic rounding and the rank key.  The expanded-attempt kernel queues
+// the surviving draws and finishes them 32 at a time, so the second half
+// runs on full warps.
+template <int K>
+__device__ __forceinline__ bool attempt_draw(const SysDev &s, const Det<K> &dj, const R4 &r, unsigned &code, int &gc)
 {
     Det<K> di;
     int nh, i, j, a, b;
-    double inv_pgen;
-    float inv_pgen_f;
-    if (!excite(s, dj, r, di, nh, i, j, a, b, inv_pgen, inv_pgen_f)) return false;
+    if (!excite(s, dj, r, di, nh, i, j, a, b, gc)) return false;
     if (level_of(s, di) > s.lmax) return false;
+    code = (unsigned)i | ((unsigned)j << 8) | ((unsigned)a << 16) | ((unsigned)b << 24);
+    return true;
+}
+
+template <int K, typename R>
+__device__ __forceinline__ bool attempt_finish(const SysDev &s, const RunParams &p, const Det<K> &dj, double c_att,
+                                               u64 r3, unsigned code, int gc, u64 &key, i64 &val, unsigned &err)
+{
+    const int i = code & 255, j = (code >> 8) & 255, a = (code >> 16) & 255, b = code >> 24;
+    const int nh = (gc == 1 || gc == 2) ? 1 : 2;
+    Det<K> di = dj;
+    flip(di, i);
+    if (nh == 2) flip(di, j);
+    flip(di, a);
+    if (nh == 2) flip(di, b);
     // matrix element and 1/p_gen in the precision R; the value itself in FP64
     double h = h_offdiag<K, R>(s, dj, nh, i, j, a, b);
-    double ipg = sizeof(R) == 4 ? (double)inv_pgen_f : inv_pgen;
-    double x = ((p.tau * h) * ipg) * c_att;
+    double x = ((p.tau * h) * inv_pgen_of<R>(s, gc)) * c_att;
     if (excitor_sign(s, di) > 0) x = -x;
     i64 v;
-    if (!round_value(x, r.v[3], p, true, v)) {
+    if (!round_value(x, r3, p, true, v)) {
         err |= ERRB_NUMERIC;
         return false;
     }
@@ -349,6 +366,69 @@ __device__ __forceinline__ bool spawn_attempt(const SysDev &s, const RunParams &
     key = rank_key(s, di);
     val = v;
     return true;
+}
+
+// Per-warp queue of drawn attempts waiting for attempt_finish.
+template <int K>
+struct AttQueue {
+    u64 det[K][64];
+    double c[64];
+    u64 r[64];
+    unsigned code[64];
+    unsigned char gc[64];
+};
+
+// All 32 lanes call; lanes with ok append their attempt (qn < 32 on entry).
+template <int K>
+__device__ __forceinline__ void q_push(AttQueue<K> &q, int &qn, bool ok, const Det<K> &dj, double c, u64 r3, unsigned code,
+                                       int gc)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(FULLMASK, ok);
+    if (ok) {
+        const int e = qn + __popc(m & ((1u << lane) - 1u));
+#pragma unroll
+        for (int w = 0; w < K; w++) q.det[w][e] = dj.w[w];
+        q.c[e] = c;
+        q.r[e] = r3;
+        q.code[e] = code;
+        q.gc[e] = (unsigned char)gc;
+    }
+    qn += __popc(m);
+    __syncwarp();
+}
+
+// All 32 lanes call: finishes the newest 32 queued attempts while 32 or more
+// are waiting (with all, every waiting attempt) and appends the records.
+template <int K, typename R>
+__device__ __forceinline__ void q_drain(AttQueue<K> &q, int &qn, bool all, const SysDev &s, const RunParams &p,
+                                        DevStep *st, const SpawnBuf &sp, unsigned &err)
+{
+    const int lane = threadIdx.x & 31;
+    while (qn >= 32 || (all && qn > 0)) {
+        const int take = qn >= 32 ? 32 : qn;
+        int nrec = 0;
+        u64 k = 0;
+        i64 v = 0;
+        if (lane < take) {
+            const int e = qn - take + lane;
+            Det<K> dj;
+#pragma unroll
+            for (int w = 0; w < K; w++) dj.w[w] = q.det[w][e];
+            if (attempt_finish<K, R>(s, p, dj, q.c[e], q.r[e], q.code[e], q.gc[e], k, v, err)) nrec = 1;
+        }
+        __syncwarp();   // the entries are read before later pushes reuse them
+        qn -= take;
+        const i64 off = warp_reserve(&st->n_sp, (i64)nrec);
+        if (nrec) {
+            if (off < sp.cap) {
+                sp.key[0][off] = k;
+                sp.pop[0][off] = v;
+            } else {
+                err |= ERRB_SPAWN_OVERFLOW;
+            }
+        }
+    }
 }
 
 // occupation threshold: 0 < |v| < 1 becomes +-1 with probability |v|, else 0
@@ -636,11 +716,16 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
                     }
                     cl_att += (double)natt;
                 } else {
+                    // one attempt, finished in place (the sampler's lanes
+                    // diverge anyway; queueing did not pay here)
                     inline_att++;
                     R4 ra = draw(p.seed, p.replica, it, TAG_SAMPLE_ATT, (u64)g, 0);
+                    unsigned code;
+                    int gc;
                     u64 k;
                     i64 v;
-                    if (spawn_attempt<K, R>(s, p, dj, coef, ra, k, v, err)) {
+                    if (attempt_draw<K>(s, dj, ra, code, gc) &&
+                        attempt_finish<K, R>(s, p, dj, coef, ra.v[3], code, gc, k, v, err)) {
                         rk[nrec] = k;
                         rv[nrec] = v;
                         nrec++;
@@ -716,6 +801,9 @@ __device__ __forceinline__ void d_attempts(const SysDev &s, const ListView &L, D
     const i64 nwarps = (i64)gridDim.x * blockDim.x / 32;
     const i64 wglob = ((i64)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     unsigned err = 0;
+    __shared__ AttQueue<K> aq[WORK_THREADS / 32];
+    AttQueue<K> &q = aq[threadIdx.x >> 5];
+    int qn = 0;   // drawn attempts waiting in this warp's queue (warp-uniform)
     for (int part = 0; part < 2; part++) {
         // part 0: full non-composite attempts (owners: list entries);
         // part 1: attempts of the composite clusters queued by k_sample
@@ -729,12 +817,13 @@ __device__ __forceinline__ void d_attempts(const SysDev &s, const ListView &L, D
         for (i64 t0 = a0; t0 < a1; t0 += 32) {
             i64 o, m;
             window_step(end, nown, t0, w, o, m);
-            int nrec = 0;
-            u64 k = 0;
-            i64 v = 0;
+            bool ok = false;
+            Det<K> dj;
+            double ca = 0.0;
+            u64 r3 = 0;
+            unsigned code = 0;
+            int gc = 0;
             if (t0 + lane < a1) {
-                Det<K> dj;
-                double ca;
                 u64 tag, idx;
                 if (part == 0) {
                     dj = load_det<K>(L.bits, L.cap, o);
@@ -748,19 +837,14 @@ __device__ __forceinline__ void d_attempts(const SysDev &s, const ListView &L, D
                     idx = cl.index[o];
                 }
                 R4 r = draw(p.seed, p.replica, it, tag, idx, (u64)m);
-                if (spawn_attempt<K, R>(s, p, dj, ca, r, k, v, err)) nrec = 1;
+                ok = attempt_draw<K>(s, dj, r, code, gc);
+                r3 = r.v[3];
             }
-            i64 off = warp_reserve(&st->n_sp, nrec);
-            if (nrec) {
-                if (off < sp.cap) {
-                    sp.key[0][off] = k;
-                    sp.pop[0][off] = v;
-                } else {
-                    err |= ERRB_SPAWN_OVERFLOW;
-                }
-            }
+            q_push<K>(q, qn, ok, dj, ca, r3, code, gc);
+            q_drain<K, R>(q, qn, false, s, p, st, sp, err);
         }
     }
+    q_drain<K, R>(q, qn, true, s, p, st, sp, err);
     if (err) atomicOr(&st->err, err);
 }
 

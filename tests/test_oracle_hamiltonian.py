@@ -118,3 +118,57 @@ def test_ueg_space_size_matches_paper(nel, nso, lmax, size):
     s = oracle.System.ueg(nel, nso, 1.0, lmax)
     # at CCSD every double is one draw from HF, so the top level need not be expanded
     assert s.generator_closure(lmax, expand_top=(lmax > 2)) == size
+
+
+def _random_excited(nel, nso, level, rng):
+    """A determinant (int bit string) with `level` holes in the lowest nel
+    spin-orbitals and `level` particles above them, any spins."""
+    holes = rng.choice(nel, size=level, replace=False)
+    parts = nel + rng.choice(nso - nel, size=level, replace=False)
+    d = (1 << nel) - 1
+    for q in list(holes) + list(parts):
+        d ^= 1 << int(q)
+    return d
+
+
+@pytest.mark.parametrize("kind", ["ueg", "molecule", "molecule41"])
+def test_excitation_form_diagonal_equals_slater_condon(kind):
+    """H_DD - E_HF in the excitation form (Fock diagonal of the reference plus
+    pair corrections among holes and particles) equals the difference of the
+    two plain Slater-Condon diagonals <D|H|D> - <HF|H|HF>, for determinants
+    of every excitation level up to 6 (spins not conserved: the identity
+    holds for any determinant)."""
+    from ccmc_inputs import molecule_integrals
+
+    rng = np.random.Generator(np.random.PCG64(17))
+    if kind == "ueg":
+        s, nel, nso = oracle.System.ueg(14, 66, 1.0, 4), 14, 66
+    elif kind == "molecule":
+        h1, eri = molecule_integrals(norb=8, nocc=3, seed=5)
+        s, nel, nso = oracle.System.generic(6, h1, eri, 4), 6, 16
+    else:
+        h1, eri = molecule_integrals(norb=41, nocc=10, seed=7)
+        s, nel, nso = oracle.System.generic(20, h1, eri, 4), 20, 82
+    hf = (1 << nel) - 1
+    ehf = s.hij(hf, hf)
+    for level in range(1, 7):
+        for _ in range(40):
+            d = _random_excited(nel, nso, min(level, nel, nso - nel), rng)
+            direct = s.hij(d, d) - ehf
+            assert abs(s.hdiag_rel(d) - direct) <= 1e-12 * max(1.0, abs(ehf)), (level, d)
+
+
+def test_excitation_form_diagonal_fp32_within_single_precision():
+    """The FP32 form of H_DD - E_HF agrees with the FP64 one to single
+    precision of the summed terms (a dozen terms of at most a few hartree)."""
+    from ccmc_inputs import molecule_integrals
+
+    rng = np.random.Generator(np.random.PCG64(18))
+    h1, eri = molecule_integrals(norb=41, nocc=10, seed=7)
+    for s, nel, nso in [(oracle.System.ueg(54, 162, 1.0, 2).set_fp32(), 54, 162),
+                        (oracle.System.generic(20, h1, eri, 4).set_fp32(), 20, 82)]:
+        for level in range(1, 5):
+            for _ in range(40):
+                d = _random_excited(nel, nso, level, rng)
+                e64, e32 = s.hdiag_rel(d), s.hdiag_rel_f(d)
+                assert abs(e32 - e64) <= 2e-6 * (1.0 + 8 * level * 25.0), (level, e64, e32)
