@@ -191,12 +191,13 @@ def slices_for(sim, per_slice=200_000):
     return max(1, (r0.n_sel + r0.n_visit + per_slice - 1) // per_slice)
 
 
-def oracle_slices(sim, n_occ, nslices, count, it0=STATE_ITER):
-    """Times `count` slices, each 1/nslices of one full step's visits and
-    cluster samples (propagation only).  Returns (samples, seconds, spawned)."""
+def oracle_slices(sim, n_occ, nslices, count, it0=STATE_ITER, first=0):
+    """Times `count` slices (numbers first, first+1, ...), each 1/nslices of
+    one full step's visits and cluster samples (propagation only).  Returns
+    (samples, seconds, spawned)."""
     samples, secs, spawned = 0, 0.0, 0
     n_sel = None
-    for k in range(count):
+    for k in range(first, first + count):
         q = k % nslices
         sim.set_state(it0 + k // nslices, STATE_SHIFT, True, 1.0)
         if n_sel is None:
@@ -212,26 +213,71 @@ def oracle_slices(sim, n_occ, nslices, count, it0=STATE_ITER):
     return samples, secs, spawned
 
 
+# one oracle per host core (processes started with spawn, after or apart
+# from any CUDA use); each builds its own full-size state, waits at a
+# barrier, then times its own slices
+_POOL_BARRIER = None
+
+
+def _pool_init(barrier):
+    global _POOL_BARRIER
+    _POOL_BARRIER = barrier
+
+
+def _pool_slices(job):
+    w, warm, count, first, per_slice = job
+    sim, n_occ = oracle_state(w)
+    nslices = slices_for(sim, per_slice)
+    if warm:
+        oracle_slices(sim, n_occ, nslices, warm, first=first)
+    _POOL_BARRIER.wait()
+    samples, secs, spawned = oracle_slices(sim, n_occ, nslices, count, first=first + warm)
+    return samples, secs, spawned, nslices
+
+
+def oracle_all_cores(w, warm: int, count: int, cores: int = 0, per_slice: int = 200_000):
+    """Every host core runs the oracle on `count` slices of its own (about
+    per_slice samples each); returns (samples/s, keys/s, cores, seconds,
+    slices of a step).  The job's rate is the summed samples over the slowest
+    process's time."""
+    import multiprocessing as mp
+
+    cores = cores or len(os.sched_getaffinity(0))
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(cores)
+    with ctx.Pool(cores, initializer=_pool_init, initargs=(barrier,)) as pool:
+        res = pool.map(_pool_slices, [(w, warm, count, c * (warm + count), per_slice) for c in range(cores)])
+    secs = max(r[1] for r in res)
+    samples = sum(r[0] for r in res)
+    spawned = sum(r[2] for r in res)
+    return samples / secs, spawned / secs, cores, secs, res[0][3]
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    # a reference "step" is one slice per process, sized so that the whole
+    # run takes about a minute of oracle time
     sim, n_occ = oracle_state(w)
-    nslices = slices_for(sim)
-    oracle_slices(sim, n_occ, nslices, args.warmup)
-    samples, secs, spawned = oracle_slices(sim, n_occ, nslices, args.steps)
-    v = samples / secs
+    n1 = slices_for(sim)
+    _, t1, _ = oracle_slices(sim, n_occ, n1, 1)
+    rate = (sim.sample_range(0, 0, 0, 0).n_sel + n_occ) / n1 / max(t1, 1e-6)
+    per_slice = max(2000, int(rate * 60.0 / max(1, args.steps + args.warmup)))
+    del sim
+    v, kps, cores, secs, nslices = oracle_all_cores(w, args.warmup, args.steps, per_slice=per_slice)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs * nslices / (args.steps * cores),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "keys_per_s": spawned / secs,
+        "keys_per_s": kps,
         "config": {"workload": w["name"], "electrons": w["nel"], "spin_orbitals": w.get("nso", 2 * w.get("norb", 0)),
                    "truncation": w["lmax"], "target_pop": w["target_pop"], "tau": w["tau"],
                    "sampling": "fnc+multispawn" if w["fnc"] else "original"},
-        "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} slices of 1/{nslices} of a full step (visits + cluster samples, "
-                                   f"propagation only) on the {state_name(w)}, N_total = target"},
+        "cpu_baseline": {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{cores} processes x {args.steps} slices of 1/{nslices} of a full step (visits + "
+                                   f"cluster samples, propagation only) on the {state_name(w)}, N_total = target; "
+                                   f"ms_per_step is the job's time per full step"},
         "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -353,15 +399,7 @@ def run_gpu(args, w):
     ms_total = sum(times)
     samples = sum(r["n_sel"] + r["n_visit"] for r in recs)
     keys = sum(r["n_spawned"] for r in recs)
-    if dist:
-        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-        c = torch.tensor([samples, keys], device="cuda", dtype=torch.float64)
-        dist.all_reduce(c)
-        samples_all, keys_all = float(c[0].item()), float(c[1].item())
-    else:
-        ms_max, samples_all, keys_all = ms_total, float(samples), float(keys)
+    ms_max, samples_all, keys_all = aggregate(dist, ms_total, samples, keys, "cuda")
 
     # per-phase timing pass (events between phases, one step at a time)
     ctx.profile(True)
@@ -444,6 +482,20 @@ def run_gpu(args, w):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def aggregate(dist, ms_total: float, samples: float, keys: float, device: str):
+    """Whole-job figures over the ranks: the slowest rank's time and the sum
+    of every rank's samples and keys (each rank steps its own replica)."""
+    if dist is None:
+        return ms_total, float(samples), float(keys)
+    import torch
+
+    t = torch.tensor([ms_total], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(samples), float(keys)], device=device, dtype=torch.float64)
+    dist.all_reduce(c)
+    return float(t.item()), float(c[0].item()), float(c[1].item())
 
 
 def read_traffic(workload: str, phase: str):
@@ -620,8 +672,9 @@ def run_gpu_batched(args):
 
 
 def cpu_baseline(w):
-    """The oracle on one host core, on slices of one full step at the target
-    size (about 10 s of CPU work)."""
+    """The oracle on slices of one full step at the target size: one core
+    (about 8 s of CPU work), then every host core with the same slice count
+    each."""
     try:
         sim, n_occ = oracle_state(w)
     except Exception as e:  # the oracle is a reported baseline only
@@ -630,9 +683,18 @@ def cpu_baseline(w):
     s1, t1, _ = oracle_slices(sim, n_occ, nslices, 1)          # calibration slice
     done = max(1, min(4 * nslices, int(8.0 / max(t1, 1e-3))))
     samples, secs, _ = oracle_slices(sim, n_occ, nslices, done)
-    return {"value": samples / secs, "unit": "samples/s", "cores": 1, "kind": "oracle",
-            "sample": f"{done} slice(s) of 1/{nslices} of a full step (visits + cluster samples, propagation only) "
-                      f"on the {state_name(w)} at N_total = target, {secs:.1f} s"}
+    one = samples / secs
+    del sim
+    try:
+        v, _, cores, psecs, _ = oracle_all_cores(w, 0, done)
+    except Exception as e:
+        return {"value": one, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                "sample": f"{done} slice(s) of 1/{nslices} of a full step on the {state_name(w)}, {secs:.1f} s "
+                          f"(all-core run unavailable: {e})"}
+    return {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes x {done} slice(s) of 1/{nslices} of a full step (visits + cluster samples, "
+                      f"propagation only) on the {state_name(w)} at N_total = target, {psecs:.1f} s",
+            "single_core": {"value": one, "cores": 1, "seconds": secs}}
 
 
 def main():
