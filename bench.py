@@ -380,6 +380,10 @@ def run_gpu(args, w):
 
     timed(args.warmup)
     ctx.records()
+    fp32 = w.get("precision") == "fp32"
+    if fp32:   # the timed window's start state, for the FP64 comparison
+        start_list = ctx.get_list()
+        start_state = ctx.get_state()
     _, _, launches0 = ctx.phase_times()
     clocks = ClockSampler(local)
     clocks.start()
@@ -449,6 +453,10 @@ def run_gpu(args, w):
     else:
         e2e_samples = sum(r["n_sel"] + r["n_visit"] for r in erecs[-e2e_steps:])
 
+    fp32_energy = None
+    if fp32:
+        fp32_energy = fp32_vs_fp64(ccmc, w, ctx, stream, start_list, start_state, min(args.steps, 200), rank)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
@@ -479,9 +487,63 @@ def run_gpu(args, w):
         "gpu_launches": int(launches1 - launches0),
         "cpu_baseline": cpu,
     }
+    if fp32_energy is not None:
+        line["fp32_energy"] = fp32_energy
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def blocked_error(x):
+    """Standard error of the mean of a correlated series: the largest
+    blocked estimate over block sizes that leave at least 8 blocks."""
+    import numpy as np
+
+    x = np.asarray(x, dtype=np.float64)
+    best, b = 0.0, 1
+    while len(x) // b >= 8:
+        m = len(x) // b
+        y = x[: m * b].reshape(m, b).mean(axis=1)
+        best = max(best, float(y.std(ddof=1) / np.sqrt(m)))
+        b *= 2
+    return best
+
+
+def fp32_vs_fp64(ccmc, w, ctx32, stream, start_list, start_state, nwin, rank):
+    """Energy error of the FP32 form against the FP64 path from the timed
+    window's start state: (1) the projected energy of single steps from the
+    identical state (same samples, so the difference is the arithmetic),
+    (2) the mean projected energy over nwin steps of each path, with blocked
+    standard errors."""
+    ctx64 = ccmc.from_workload(w, replica=rank, stream=stream.cuda_stream, precision="fp64")
+    bits, _, pop = start_list
+    it0, shift0, vary0, nprev0 = start_state
+
+    def e_proj(r):
+        return r["e_num"] / (r["n0"] / 65536.0) if r["n0"] else 0.0
+
+    one = []
+    for k in range(4):
+        e = []
+        for c in (ctx32, ctx64):
+            c.records()
+            c.set_list(bits, pop)
+            c.set_state(it0 + k, shift0, vary0, nprev0)
+            c.step(1)
+            e.append(e_proj(c.records()[-1]))
+        one.append(abs(e[0] - e[1]) / max(abs(e[1]), 1e-300))
+    means = []
+    for c in (ctx32, ctx64):
+        c.records()
+        c.set_list(bits, pop)
+        c.set_state(it0, shift0, vary0, nprev0)
+        c.step(nwin)
+        ser = [e_proj(r) for r in c.records()[-nwin:]]
+        means.append((sum(ser) / len(ser), blocked_error(ser)))
+    ctx64.close()
+    return {"one_step_rel_diff_max": max(one), "one_step_steps": len(one), "window_steps": nwin,
+            "e_proj_fp32": means[0][0], "err_fp32": means[0][1], "e_proj_fp64": means[1][0],
+            "err_fp64": means[1][1], "diff": means[0][0] - means[1][0]}
 
 
 def aggregate(dist, ms_total: float, samples: float, keys: float, device: str):
