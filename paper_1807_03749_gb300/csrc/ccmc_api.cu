@@ -455,6 +455,9 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     for (int g = 0; g < 2; g++) s.inv_pgen_single_f[g] = (float)h.inv_pgen_single[g];
     for (int c = 0; c < 3; c++) s.inv_pgen_double_f[c] = (float)h.inv_pgen_double[c];
     s.cocc = h.cocc;
+    // smallest excitation level a list entry can have: the gas sector has no
+    // single excitations (momentum), the molecule has them
+    s.lmin_exc = h.kind == CCMC_UEG ? 2 : 1;
 
     RunParams &rp = ctx->sc.prm;
     rp.tau = params->tau;
@@ -610,15 +613,32 @@ ccmc_status ccmc_set_list(ccmc_ctx *ctx, const uint64_t *bits, const int64_t *po
     if ((i64)n > ctx->list_cap) return fail(ctx, CCMC_ERR_LIST_OVERFLOW, "list larger than list_capacity");
     const HostSys &h = ctx->hs;
     const int K = h.nw;
-    // validate: popcount N, level <= l, first entry HF
+    // validate: popcount N, level <= l, first entry HF, the reference's S_z
+    // and (gas) its total momentum: the sector every spawn stays in, so a
+    // gas list has no single excitations
+    const u64 alpha = 0x5555555555555555ULL;
+    int na_hf = 0;
+    for (int w = 0; w < K; w++) na_hf += __builtin_popcountll(ctx->sc.sys.hf[w] & alpha);
     for (size_t i = 0; i < n; i++) {
-        int pc = 0, holes = 0;
+        int pc = 0, holes = 0, na = 0, kx = 0, ky = 0, kz = 0;
         for (int w = 0; w < K; w++) {
-            pc += __builtin_popcountll(bits[i * K + w]);
-            holes += __builtin_popcountll(ctx->sc.sys.hf[w] & ~bits[i * K + w]);
-            if (bits[i * K + w] & ~ctx->sc.sys.valid[w]) return fail(ctx, CCMC_ERR_ARG, "orbital beyond M");
+            const u64 x = bits[i * K + w];
+            pc += __builtin_popcountll(x);
+            na += __builtin_popcountll(x & alpha);
+            holes += __builtin_popcountll(ctx->sc.sys.hf[w] & ~x);
+            if (x & ~ctx->sc.sys.valid[w]) return fail(ctx, CCMC_ERR_ARG, "orbital beyond M");
+            if (h.kind == CCMC_UEG)
+                for (u64 m = x; m; m &= m - 1) {
+                    const int q = (64 * w + __builtin_ctzll(m)) >> 1;
+                    kx += h.kv[3 * q];
+                    ky += h.kv[3 * q + 1];
+                    kz += h.kv[3 * q + 2];
+                }
         }
         if (pc != h.nel) return fail(ctx, CCMC_ERR_ARG, "wrong electron count");
+        if (na != na_hf) return fail(ctx, CCMC_ERR_ARG, "determinant outside the reference's S_z sector");
+        if (kx != 0 || ky != 0 || kz != 0)
+            return fail(ctx, CCMC_ERR_ARG, "determinant outside the zero-momentum sector");
         if (holes > h.lmax) return fail(ctx, CCMC_ERR_ARG, "excitor beyond the truncation level");
         if (i == 0 && holes != 0) return fail(ctx, CCMC_ERR_ARG, "first entry must be HF");
     }

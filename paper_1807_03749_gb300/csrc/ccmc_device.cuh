@@ -68,6 +68,7 @@ struct SysDev {
     // rank key: tab[c * RANK_STRIDE + q] = sum_{j=0}^{l-c} C(q, j)
     const u64 *rank_tab;
     u64 cocc;
+    int lmin_exc;        // smallest excitation level of any non-reference list entry
     const double *fock;  // reference Fock diagonal per spin-orbital
     // FP32 form: tables rounded from the FP64 ones
     const float *tkin_f, *vtab_f, *h1_f, *eri_f;

@@ -653,7 +653,10 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
             dj = hf_det<K>(s);
             if (sz == 0) {
                 amp = n0 < 0 ? -smag[0] : smag[0];
-            } else if (nex == 0 || (sz >= 2 && n0 == 0)) {
+            } else if (nex == 0 || (sz >= 2 && n0 == 0) || sz * s.lmin_exc > s.lmax + 2) {
+                // the last test: a valid cluster's level is the sum of its
+                // excitors' levels, so this size cannot stay within l + 2
+                // and the sample contributes nothing (its picks are skipped)
                 valid = false;
             } else {
                 R4 r1;

@@ -373,6 +373,12 @@ def test_rejects_bad_lists(ccmc):
     d = ((1 << 14) - 1) ^ 0b11 ^ (0b11 << 14)
     with pytest.raises(ccmc.CCMCError):
         ctx.set_list(np.array([[d], [(1 << 14) - 1]], dtype=np.uint64), np.array([65536, 65536]))  # HF not first
+    single = ((1 << 14) - 1) ^ (1 << 12) ^ (1 << 14)   # alpha 6 -> alpha 7: momentum changes
+    with pytest.raises(ccmc.CCMCError):
+        ctx.set_list(np.array([[(1 << 14) - 1], [single]], dtype=np.uint64), np.array([65536, 65536]))
+    flip = ((1 << 14) - 1) ^ (1 << 13) ^ (1 << 14)      # beta hole, alpha particle: S_z changes
+    with pytest.raises(ccmc.CCMCError):
+        ctx.set_list(np.array([[(1 << 14) - 1], [flip]], dtype=np.uint64), np.array([65536, 65536]))
     ctx.set_list(hf, np.array([100 * 65536]))
 
 
