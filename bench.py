@@ -428,7 +428,10 @@ def run_gpu(args, w):
     # list, one step, download the list and the estimators
     if restore is not None:
         restore()
-    bits, _, pop = ctx.get_list()
+    n_now = ctx.list_size()
+    cap = 4 * n_now + 65536
+    bufs = [pinned_list_buffers(cap, ctx.nw) for _ in range(2)]
+    bits, _, pop = ctx.get_list(out=bufs[0])
     e2e_steps = args.e2e_steps
     h2d = d2h = 0
     e2e_samples = 0
@@ -440,7 +443,7 @@ def run_gpu(args, w):
             ctx.set_state(STATE_ITER, STATE_SHIFT, 1, ntot0)
         h2d += bits.nbytes + pop.nbytes
         ctx.step(1)
-        out_bits, keys_h, out_pop = ctx.get_list()
+        out_bits, keys_h, out_pop = ctx.get_list(out=bufs[(k + 1) % 2])
         en = ctx.energy()
         d2h += out_bits.nbytes + keys_h.nbytes + out_pop.nbytes + 40
         if restore is None:
@@ -492,6 +495,17 @@ def run_gpu(args, w):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def pinned_list_buffers(cap: int, nw: int):
+    """Page-locked host arrays for a list of up to cap entries:
+    (bits[cap, nw] uint64, keys[cap] uint64, pop[cap] int64)."""
+    import torch
+
+    bits = torch.empty((cap, nw), dtype=torch.int64, pin_memory=True).numpy().view("uint64")
+    keys = torch.empty(cap, dtype=torch.int64, pin_memory=True).numpy().view("uint64")
+    pop = torch.empty(cap, dtype=torch.int64, pin_memory=True).numpy()
+    return bits, keys, pop
 
 
 def blocked_error(x):
@@ -687,7 +701,8 @@ def run_gpu_batched(args):
 
     # end to end: every replica's list from host memory, one batched step,
     # every list and estimator back to the host
-    lists = [c.get_list() for c in ctxs]
+    bufs = [[pinned_list_buffers(4 * c.list_size() + 65536, c.nw) for c in ctxs] for _ in range(2)]
+    lists = [c.get_list(out=b) for c, b in zip(ctxs, bufs[0])]
     h2d = d2h = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -696,7 +711,7 @@ def run_gpu_batched(args):
             c.set_list(bits, pop)
             h2d += bits.nbytes + pop.nbytes
         batch.step(1)
-        lists = [c.get_list() for c in ctxs]
+        lists = [c.get_list(out=b) for c, b in zip(ctxs, bufs[(k + 1) % 2])]
         for c, (bits, kk, pop) in zip(ctxs, lists):
             c.energy()
             d2h += bits.nbytes + kk.nbytes + pop.nbytes + 40

@@ -217,6 +217,10 @@ struct ccmc_ctx {
     // captured CUDA graph of one step (replayed on non-NULL streams)
     cudaGraphExec_t graph = nullptr;
     i64 graph_launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // list upload/download: row-major determinants (K words per entry) and
+    // the validation word of the last upload
+    u64 *io = nullptr;
+    unsigned *d_bad = nullptr, *h_bad = nullptr;
 };
 
 namespace {
@@ -251,35 +255,109 @@ ccmc_status status_from_bits(ccmc_ctx *ctx, unsigned bits)
     return CCMC_OK;
 }
 
-// device helper kernels for list upload: keys and diagonal energies
+// validation bits of an uploaded list
+enum : unsigned {
+    BAD_COUNT = 1u, BAD_RANGE = 2u, BAD_SZ = 4u, BAD_MOMENTUM = 8u, BAD_LEVEL = 16u, BAD_FIRST = 32u, BAD_ORDER = 64u
+};
+
+// Uploaded list: row-major determinants -> the list's word-major layout,
+// each entry checked (electron count, orbital range, the reference's S_z,
+// zero total momentum for the gas, truncation level, HF first), then its
+// key and diagonal energy.
 template <int K, typename R>
-__global__ void k_prepare_list(SysDev s, ListView L, i64 n)
+__global__ void k_load_list(SysDev s, ListView L, const u64 *rows, i64 n, unsigned *bad)
 {
+    const u64 alpha = 0x5555555555555555ULL;
+    unsigned b = 0;
     for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
         Det<K> d;
-        for (int w = 0; w < K; w++) d.w[w] = L.bits[w * L.cap + i];
-        L.key[i] = rank_key(s, d);
-        L.diag[i] = is_hf(s, d) ? 0.0 : diag_rel<K, R>(s, d);
+        int pc = 0, na = 0, holes = 0, kx = 0, ky = 0, kz = 0;
+        unsigned e = 0;
+#pragma unroll
+        for (int w = 0; w < K; w++) {
+            const u64 x = rows[i * K + w];
+            d.w[w] = x;
+            L.bits[w * L.cap + i] = x;
+            pc += __popcll(x);
+            na += __popcll(x & alpha);
+            holes += __popcll(s.hf[w] & ~x);
+            if (x & ~s.valid[w]) e |= BAD_RANGE;
+            if (s.kind == 0)
+                for (u64 m = x & s.valid[w]; m; m &= m - 1) {
+                    const int q = (64 * w + __ffsll((long long)m) - 1) >> 1;
+                    kx += __ldg(&s.kv[3 * q]);
+                    ky += __ldg(&s.kv[3 * q + 1]);
+                    kz += __ldg(&s.kv[3 * q + 2]);
+                }
+        }
+        int na_ref = 0;
+#pragma unroll
+        for (int w = 0; w < K; w++) na_ref += __popcll(s.hf[w] & alpha);
+        if (pc != s.nel) e |= BAD_COUNT;
+        if (na != na_ref) e |= BAD_SZ;
+        if (kx != 0 || ky != 0 || kz != 0) e |= BAD_MOMENTUM;
+        if (holes > s.lmax) e |= BAD_LEVEL;
+        if (i == 0 && holes != 0) e |= BAD_FIRST;
+        if (e == 0) {
+            L.key[i] = rank_key(s, d);
+            L.diag[i] = holes == 0 ? 0.0 : diag_rel<K, R>(s, d);
+        } else {
+            L.key[i] = 0;
+            L.diag[i] = 0.0;
+        }
+        b |= e;
     }
+    if (b) atomicOr(bad, b);
 }
 
-cudaError_t prepare_list(ccmc_ctx *ctx, ListView &L, i64 n)
+__global__ void k_check_order(const u64 *key, i64 n, unsigned *bad)
 {
-    int g = (int)std::min<i64>(4096, (n + 255) / 256 + 1);
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x + 1; i < n; i += (i64)gridDim.x * blockDim.x)
+        if (key[i] <= key[i - 1]) {
+            atomicOr(bad, (unsigned)BAD_ORDER);
+            return;
+        }
+}
+
+// the list in row-major order for download
+template <int K>
+__global__ void k_store_list(ListView L, u64 *rows, i64 n)
+{
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int w = 0; w < K; w++) rows[i * K + w] = L.bits[w * L.cap + i];
+}
+
+cudaError_t load_list(ccmc_ctx *ctx, ListView &L, i64 n)
+{
+    const int g = (int)std::min<i64>(4096, (n + 255) / 256 + 1);
     const bool f = ctx->sc.fp32;
+    cudaStream_t sm = ctx->stream;
     switch (ctx->sc.K) {
     case 1:
-        if (f) k_prepare_list<1, float><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n);
-        else k_prepare_list<1, double><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n);
+        if (f) k_load_list<1, float><<<g, 256, 0, sm>>>(ctx->sc.sys, L, ctx->io, n, ctx->d_bad);
+        else k_load_list<1, double><<<g, 256, 0, sm>>>(ctx->sc.sys, L, ctx->io, n, ctx->d_bad);
         break;
     case 2:
-        if (f) k_prepare_list<2, float><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n);
-        else k_prepare_list<2, double><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n);
+        if (f) k_load_list<2, float><<<g, 256, 0, sm>>>(ctx->sc.sys, L, ctx->io, n, ctx->d_bad);
+        else k_load_list<2, double><<<g, 256, 0, sm>>>(ctx->sc.sys, L, ctx->io, n, ctx->d_bad);
         break;
     default:
-        if (f) k_prepare_list<3, float><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n);
-        else k_prepare_list<3, double><<<g, 256, 0, ctx->stream>>>(ctx->sc.sys, L, n);
+        if (f) k_load_list<3, float><<<g, 256, 0, sm>>>(ctx->sc.sys, L, ctx->io, n, ctx->d_bad);
+        else k_load_list<3, double><<<g, 256, 0, sm>>>(ctx->sc.sys, L, ctx->io, n, ctx->d_bad);
         break;
+    }
+    k_check_order<<<g, 256, 0, sm>>>(L.key, n, ctx->d_bad);
+    return cudaGetLastError();
+}
+
+cudaError_t store_list(ccmc_ctx *ctx, const ListView &L, i64 n)
+{
+    const int g = (int)std::min<i64>(4096, (n + 255) / 256 + 1);
+    switch (ctx->sc.K) {
+    case 1: k_store_list<1><<<g, 256, 0, ctx->stream>>>(L, ctx->io, n); break;
+    case 2: k_store_list<2><<<g, 256, 0, ctx->stream>>>(L, ctx->io, n); break;
+    default: k_store_list<3><<<g, 256, 0, ctx->stream>>>(L, ctx->io, n); break;
     }
     return cudaGetLastError();
 }
@@ -548,6 +626,8 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     wa.hist = al.arr<unsigned>((size_t)(1 << MAX_DIGIT_BITS) * sh.sort_grid);
     wa.hist_tot = al.arr<unsigned>((size_t)(1 << MAX_DIGIT_BITS));
     wa.ring = al.arr<Record>(RING);
+    ctx->io = al.arr<u64>((size_t)K * (size_t)lc);
+    ctx->d_bad = al.arr<unsigned>(1);
     ctx->sc.st = al.arr<DevStep>(1);
     ctx->sc.d_args = al.arr<StepArgs>(1);
     if (al.failed) {
@@ -556,9 +636,9 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
         return CCMC_ERR_OOM;
     }
     if (cudaMallocHost(&ctx->h_st, sizeof(DevStep)) != cudaSuccess ||
-        cudaMallocHost(&ctx->h_shift, sizeof(double)) != cudaSuccess) {
-        al.release();
-        delete ctx;
+        cudaMallocHost(&ctx->h_shift, sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_bad, sizeof(unsigned)) != cudaSuccess) {
+        ccmc_free(ctx);
         return CCMC_ERR_OOM;
     }
     ctx->sc.stream = ctx->stream;
@@ -611,51 +691,29 @@ ccmc_status ccmc_set_list(ccmc_ctx *ctx, const uint64_t *bits, const int64_t *po
 {
     if (!ctx || !bits || !pop || n < 1) return fail(ctx, CCMC_ERR_ARG, "empty list");
     if ((i64)n > ctx->list_cap) return fail(ctx, CCMC_ERR_LIST_OVERFLOW, "list larger than list_capacity");
-    const HostSys &h = ctx->hs;
-    const int K = h.nw;
-    // validate: popcount N, level <= l, first entry HF, the reference's S_z
-    // and (gas) its total momentum: the sector every spawn stays in, so a
-    // gas list has no single excitations
-    const u64 alpha = 0x5555555555555555ULL;
-    int na_hf = 0;
-    for (int w = 0; w < K; w++) na_hf += __builtin_popcountll(ctx->sc.sys.hf[w] & alpha);
-    for (size_t i = 0; i < n; i++) {
-        int pc = 0, holes = 0, na = 0, kx = 0, ky = 0, kz = 0;
-        for (int w = 0; w < K; w++) {
-            const u64 x = bits[i * K + w];
-            pc += __builtin_popcountll(x);
-            na += __builtin_popcountll(x & alpha);
-            holes += __builtin_popcountll(ctx->sc.sys.hf[w] & ~x);
-            if (x & ~ctx->sc.sys.valid[w]) return fail(ctx, CCMC_ERR_ARG, "orbital beyond M");
-            if (h.kind == CCMC_UEG)
-                for (u64 m = x; m; m &= m - 1) {
-                    const int q = (64 * w + __builtin_ctzll(m)) >> 1;
-                    kx += h.kv[3 * q];
-                    ky += h.kv[3 * q + 1];
-                    kz += h.kv[3 * q + 2];
-                }
-        }
-        if (pc != h.nel) return fail(ctx, CCMC_ERR_ARG, "wrong electron count");
-        if (na != na_hf) return fail(ctx, CCMC_ERR_ARG, "determinant outside the reference's S_z sector");
-        if (kx != 0 || ky != 0 || kz != 0)
-            return fail(ctx, CCMC_ERR_ARG, "determinant outside the zero-momentum sector");
-        if (holes > h.lmax) return fail(ctx, CCMC_ERR_ARG, "excitor beyond the truncation level");
-        if (i == 0 && holes != 0) return fail(ctx, CCMC_ERR_ARG, "first entry must be HF");
-    }
+    const int K = ctx->hs.nw;
+    // upload, then check every entry on the device: electron count, orbital
+    // range, the reference's S_z and (gas) its total momentum -- the sector
+    // every spawn stays in, so a gas list has no single excitations --,
+    // truncation level, HF first, strictly increasing keys.  The upload goes
+    // to the spare list buffer, which becomes current only if it passes.
+    const int nb = ctx->sc.cur ^ 1;
+    ListView &L = ctx->sc.list[nb];
+    CK(cudaMemsetAsync(ctx->d_bad, 0, sizeof(unsigned), ctx->stream));
+    CK(cudaMemcpyAsync(ctx->io, bits, n * (size_t)K * sizeof(u64), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(L.pop, pop, n * sizeof(i64), cudaMemcpyHostToDevice, ctx->stream));
+    CK(load_list(ctx, L, (i64)n));
+    CK(cudaMemcpyAsync(ctx->h_bad, ctx->d_bad, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    ListView &L = ctx->sc.list[ctx->sc.cur];
-    std::vector<u64> soa((size_t)K * n);
-    for (size_t i = 0; i < n; i++)
-        for (int w = 0; w < K; w++) soa[(size_t)w * n + i] = bits[i * K + w];
-    for (int w = 0; w < K; w++)
-        CK(cudaMemcpy(L.bits + (size_t)w * L.cap, soa.data() + (size_t)w * n, n * sizeof(u64), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(L.pop, pop, n * sizeof(i64), cudaMemcpyHostToDevice));
-    CK(prepare_list(ctx, L, (i64)n));
-    CK(cudaStreamSynchronize(ctx->stream));
-    std::vector<u64> keys(n);
-    CK(cudaMemcpy(keys.data(), L.key, n * sizeof(u64), cudaMemcpyDeviceToHost));
-    for (size_t i = 1; i < n; i++)
-        if (keys[i] <= keys[i - 1]) return fail(ctx, CCMC_ERR_ARG, "list not sorted and unique");
+    const unsigned bad = *ctx->h_bad;
+    if (bad & BAD_COUNT) return fail(ctx, CCMC_ERR_ARG, "wrong electron count");
+    if (bad & BAD_RANGE) return fail(ctx, CCMC_ERR_ARG, "orbital beyond M");
+    if (bad & BAD_SZ) return fail(ctx, CCMC_ERR_ARG, "determinant outside the reference's S_z sector");
+    if (bad & BAD_MOMENTUM) return fail(ctx, CCMC_ERR_ARG, "determinant outside the zero-momentum sector");
+    if (bad & BAD_LEVEL) return fail(ctx, CCMC_ERR_ARG, "excitor beyond the truncation level");
+    if (bad & BAD_FIRST) return fail(ctx, CCMC_ERR_ARG, "first entry must be HF");
+    if (bad & BAD_ORDER) return fail(ctx, CCMC_ERR_ARG, "list not sorted and unique");
+    ctx->sc.cur = nb;
     DevStep st;
     memset(&st, 0, sizeof(st));
     st.iter = ctx->iter;
@@ -852,14 +910,12 @@ ccmc_status ccmc_get_list(ccmc_ctx *ctx, uint64_t *bits, uint64_t *keys, int64_t
     const ListView &L = ctx->sc.list[ctx->sc.cur];
     const int K = ctx->hs.nw;
     if (bits) {
-        std::vector<u64> soa((size_t)K * m);
-        for (int w = 0; w < K; w++)
-            CK(cudaMemcpy(soa.data() + (size_t)w * m, L.bits + (size_t)w * L.cap, m * sizeof(u64), cudaMemcpyDeviceToHost));
-        for (size_t i = 0; i < m; i++)
-            for (int w = 0; w < K; w++) bits[i * K + w] = soa[(size_t)w * m + i];
+        CK(store_list(ctx, L, (i64)m));
+        CK(cudaMemcpyAsync(bits, ctx->io, m * (size_t)K * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
     }
-    if (keys) CK(cudaMemcpy(keys, L.key, m * sizeof(u64), cudaMemcpyDeviceToHost));
-    if (pop) CK(cudaMemcpy(pop, L.pop, m * sizeof(i64), cudaMemcpyDeviceToHost));
+    if (keys) CK(cudaMemcpyAsync(keys, L.key, m * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
+    if (pop) CK(cudaMemcpyAsync(pop, L.pop, m * sizeof(i64), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     return CCMC_OK;
 }
 
@@ -991,6 +1047,7 @@ void ccmc_free(ccmc_ctx *ctx)
         if (ctx->sc.events[e]) cudaEventDestroy(ctx->sc.events[e]);
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
     if (ctx->h_shift) cudaFreeHost(ctx->h_shift);
+    if (ctx->h_bad) cudaFreeHost(ctx->h_bad);
     delete ctx;
 }
 
