@@ -57,6 +57,8 @@ struct DevStep {
     i64 n_occ;          // list size at the start of the step
     i64 ntot, n0, nex, n_sel, fnc_attempts;
     double mag[8];      // |A_s| of a cluster of size s
+    double cmag[8];     // |A_s| / n_att(s): magnitude of one attempt's coefficient
+    i64 natt_s[8];      // attempts of a cluster of size s
     int bucket_shift;   // selection buckets cover 2^bucket_shift positions each
     int pad0;
     i64 nbuckets;
@@ -91,6 +93,7 @@ struct ClusterBuf {
 // Per-step work arrays over the list and the merge.
 struct WorkArrays {
     i64 *prefix;      // inclusive |pop| prefix over entries >= 1 (entry 0: 0)
+    double *tdeath;   // tau (Delta E_i - S) per entry (the death factor of this step)
     int *bucket;      // owner of the first position of each selection bucket
     int bucket_bits;  // log2 of the bucket capacity
     i64 *att_end;     // inclusive prefix of full non-composite attempts

@@ -530,6 +530,13 @@ __device__ __forceinline__ void d_scan_top(const ListView &L, DevStep *st, const
             den = den * fact;
             st->mag[s] = num / den;
         }
+        // every cluster of size s has |A| = mag[s]: its attempt count and
+        // the magnitude of one attempt's coefficient, once per step
+        for (int s = 0; s < 8; s++) {
+            const i64 na = attempts_of(st->mag[s], p);
+            st->natt_s[s] = na;
+            st->cmag[s] = na > 1 ? st->mag[s] / (double)na : st->mag[s];
+        }
         st->n_sp = 0;
         st->cl_packed = 0;
         st->cl_att = 0.0;
@@ -575,6 +582,8 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
                 for (u64 b = b0; b < b1; b++) wa.bucket[b] = (int)i;
             }
             wa.acc[i] = 0;
+            const double td = p.tau * ((i == 0 ? 0.0 : L.diag[i]) - S);
+            wa.tdeath[i] = td;
             i64 dv = 0;
             if (p.fnc) {
                 wa.att_end[i] = ca + ia;
@@ -584,8 +593,7 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
                 int lev = level_of(s, d);
                 if (lev == 1 || lev == 2) es.add(to_fix(h_ref<K, R>(s, d) * coef));
                 R4 r = draw(p.seed, p.replica, it, TAG_VISIT, (u64)i, 0);
-                double dE = i == 0 ? 0.0 : L.diag[i];
-                double x = (p.tau * (dE - S)) * coef;
+                double x = td * coef;
                 if (sd > 0) x = -x;
                 if (!round_value(x, r.v[0], p, false, dv)) err |= ERRB_NUMERIC;
                 wa.catt[i] = na > 1 ? coef / (double)na : coef;
@@ -612,13 +620,18 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
                                                          const SpawnBuf &sp, const ClusterBuf &cl, int enum_base,
                                                          int vb, int vg)
 {
-    __shared__ double smag[8];
+    __shared__ double smag[8], scmag[8];
+    __shared__ i64 snatt[8];
     __shared__ u64 smf[64];
     __shared__ i64 sm[32];
     __shared__ u64 smu[32];
     __shared__ i64 s_base;
     __shared__ u64 s_ubase;
-    if (threadIdx.x < 8) smag[threadIdx.x] = st->mag[threadIdx.x];
+    if (threadIdx.x < 8) {
+        smag[threadIdx.x] = st->mag[threadIdx.x];
+        scmag[threadIdx.x] = st->cmag[threadIdx.x];
+        snatt[threadIdx.x] = st->natt_s[threadIdx.x];
+    }
     __syncthreads();
     const i64 n_sel = st->n_sel, n = st->n_occ, nex = st->nex, n0 = st->n0;
     const int bshift = st->bucket_shift;
@@ -628,7 +641,7 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
     Fix128 es = {0, 0};
     unsigned err = 0;
     i64 inline_att = 0;
-    double cl_att = 0.0;   // attempts of the clusters this thread buffers
+    u64 cl_att = 0;        // attempts of the clusters this thread buffers
     i64 death_hf = 0;   // reference-cluster deaths, summed per block at the end
     // block-uniform loop: appends are reserved with one atomic per block
     // (per-warp atomics on one counter contend at 1e8 samples per step)
@@ -689,8 +702,7 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
                 if (lev == 1 || lev == 2) es.add(to_fix(h_ref<K, R>(s, dj) * coef));
                 int sdj = excitor_sign(s, dj);
                 if (sz <= 1) {
-                    double dE = sz == 0 ? 0.0 : L.diag[idx0];
-                    double x = (p.tau * (dE - S)) * coef;
+                    double x = wa.tdeath[idx0] * coef;   // tau (Delta E - S) C (idx0 = 0 for the reference)
                     if (sdj > 0) x = -x;
                     i64 dv;
                     if (!round_value(x, r0.v[1], p, false, dv)) err |= ERRB_NUMERIC;
@@ -709,15 +721,16 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
                         nrec++;
                     }
                 }
-                natt = attempts_of(fabs(amp), p);
+                natt = snatt[sz];   // = attempts_of(|amp|): |amp| = mag[sz] for every cluster of size sz
                 if (p.multispawn) {
                     push = true;
-                    catt = natt > 1 ? coef / (double)natt : coef;
+                    // coef / natt: the same division, done once per size
+                    catt = natt > 1 ? (coef < 0.0 ? -scmag[sz] : scmag[sz]) : coef;
                     if (natt > p.work_cap) {   // runaway: the attempts kernel will not run them
                         err |= ERRB_RUNAWAY;
                         natt = p.work_cap + 1;
                     }
-                    cl_att += (double)natt;
+                    cl_att += (u64)natt;
                 } else {
                     // one attempt, finished in place (the sampler's lanes
                     // diverge anyway; queueing did not pay here)
@@ -768,8 +781,8 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
     death_hf = block_sum(death_hf, sm);
     if (p.multispawn) {
         __shared__ double smd[32];
-        cl_att = block_sum(cl_att, smd);
-        if (threadIdx.x == 0 && cl_att != 0.0) atomicAdd(&st->cl_att, cl_att);
+        double ca = block_sum((double)cl_att, smd);
+        if (threadIdx.x == 0 && ca != 0.0) atomicAdd(&st->cl_att, ca);
     }
     if (threadIdx.x == 0) {
         if (death_hf) atomicAdd((unsigned long long *)&wa.death[0], (unsigned long long)death_hf);
