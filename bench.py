@@ -422,7 +422,7 @@ def run_gpu(args, w):
     alg = algorithmic_bytes(dom, precs, ctx.nw)
     hbm, src = peaks()
     achieved = alg / (dom_ms * 1e-3) / 1e9
-    traffic = read_traffic(w["name"], dom)
+    traffic, issue = read_traffic(w["name"], dom)
 
     # end-to-end through the public API with host buffers: upload the excip
     # list, one step, download the list and the estimators
@@ -482,6 +482,9 @@ def run_gpu(args, w):
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas{world}"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
+                     "sm_issue_active_pct_ncu": issue,
+                     "note": "the sampling and attempt kernels gather from L2-resident lists and are bound by integer "
+                             "issue rate; their HBM fraction is low by construction",
                      "phase_ms_per_step": {k: v / max(1, args.profile_steps) for k, v in pms.items()},
                      "algorithmic_bytes_per_launch": alg},
         "clocks": clk,
@@ -575,17 +578,17 @@ def aggregate(dist, ms_total: float, samples: float, keys: float, device: str):
 
 
 def read_traffic(workload: str, phase: str):
-    """DRAM bytes per launch of a phase's kernel from the committed ncu summary
-    (profiles/traffic_<workload>.txt), or None."""
+    """(DRAM bytes per launch, SM issue-active %) of a phase's kernel from the
+    committed ncu summary (profiles/traffic_<workload>.txt), or (None, None)."""
     path = os.path.join(ROOT, "profiles", f"traffic_{workload}.txt")
     try:
         for line in open(path):
             f = line.split()
-            if len(f) == 3 and not line.startswith("#") and f[0] == phase:
-                return float(f[2])
+            if len(f) >= 3 and not line.startswith("#") and f[0] == phase:
+                return float(f[2]), (float(f[3]) if len(f) > 3 else None)
     except OSError:
         pass
-    return None
+    return None, None
 
 
 def run_gpu_batched(args):
