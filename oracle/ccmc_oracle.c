@@ -24,6 +24,13 @@
  *   Sec. II                 shift held then varied to keep the population stable
  *   Sec. IV.B               full non-composite (FNC) sampling
  *   Sec. IV.C, Eq. 7-8      multi-spawn: n_attempts = max(1, floor(A/A_thresh))
+ *
+ * Diagonal energies H_DD - E_HF use the excitation form (reference Fock
+ * diagonal plus pair corrections among holes and particles), pinned against
+ * the plain Slater-Condon diagonal.  The FP32 mode (matrix elements,
+ * diagonal energies and 1/p_gen in single precision from tables rounded from
+ * FP64) is a convention shared with the CUDA path; its energies are pinned
+ * only to an accuracy band: parity unpinned for the FP32 energies.
  */
 #include <math.h>
 #include <stdint.h>
