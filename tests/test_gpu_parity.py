@@ -136,6 +136,32 @@ def test_ueg114_long_lockstep_and_determinism(ccmc):
             _same_list(sim, ctx)
 
 
+def test_ueg114_lockstep_from_gpu_checkpoints(ccmc):
+    """The 114 spin-orbital FNC + multi-spawn run in the production launch
+    configuration (captured CUDA graph on a stream): the GPU state at steps
+    1000 and 1980 (list, iteration, shift) is handed to the oracle, and the
+    next 20 steps of both agree bit for bit."""
+    torch = pytest.importorskip("torch")
+    w = workload("ueg14_m114_ccsdt_fnc_ms")
+    so, sim, _ = _pair(ccmc, w)
+    stream = torch.cuda.Stream()
+    ctx = ccmc.from_workload(w, stream=stream.cuda_stream)
+    done = 0
+    for start in (1000, 1980):
+        ctx.step(start - done)
+        bits, _, pop = ctx.get_list()
+        it, shift, vary, nprev = ctx.get_state()
+        sim.set_list_words(bits, pop)
+        sim.set_state(it, shift, bool(vary), nprev)
+        ctx.records()
+        for _ in range(20):
+            rec = sim.step()
+            ctx.step(1)
+            _same_record(rec, ctx.records()[-1])
+        _same_list(sim, ctx)
+        done = start + 20
+
+
 def _full_space_state(so, lmax, n_total, seed):
     keys = so.space_keys(lmax, expand_top=False)
     dets = [so.unrank(int(k)) for k in keys]
