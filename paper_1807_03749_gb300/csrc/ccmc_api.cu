@@ -611,6 +611,7 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     const i64 lc = ctx->list_cap;
     wa.prefix = al.arr<i64>(lc);
     wa.tdeath = al.arr<double>(lc);
+    wa.href = al.arr<double>(lc);
     wa.bucket_bits = 10;
     while (wa.bucket_bits < 22 && (1LL << wa.bucket_bits) < lc / 2) wa.bucket_bits++;
     wa.bucket = al.arr<int>(((size_t)1 << wa.bucket_bits) + 1);

@@ -94,6 +94,7 @@ struct ClusterBuf {
 struct WorkArrays {
     i64 *prefix;      // inclusive |pop| prefix over entries >= 1 (entry 0: 0)
     double *tdeath;   // tau (Delta E_i - S) per entry (the death factor of this step)
+    double *href;     // <HF|H|D_i> per entry (levels 1-2; 0 otherwise), without full non-composite sampling
     int *bucket;      // owner of the first position of each selection bucket
     int bucket_bits;  // log2 of the bucket capacity
     i64 *att_end;     // inclusive prefix of full non-composite attempts

@@ -597,6 +597,11 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
                 if (sd > 0) x = -x;
                 if (!round_value(x, r.v[0], p, false, dv)) err |= ERRB_NUMERIC;
                 wa.catt[i] = na > 1 ? coef / (double)na : coef;
+            } else {
+                // <HF|H|D_i> for the single-excitor clusters of the sampler
+                const Det<K> d = load_det<K>(L.bits, L.cap, i);
+                const int lev = level_of(s, d);
+                wa.href[i] = (lev == 1 || lev == 2) ? h_ref<K, R>(s, d) : 0.0;
             }
             wa.death[i] = dv;
         }
@@ -684,11 +689,20 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
                 for (int e = 1; e < sz; e++)
                     for (int f = 0; f < e; f++)
                         if (idx[f] == idx[e]) valid = false;   // repeated excitor: discarded
-                for (int e = 0; e < sz && valid; e++) {
-                    const i64 id = idx[e];
+                if (sz == 1) {
+                    // one excitor: its own determinant, with the sign s_D of
+                    // applying it to HF (the closed form of the same product)
+                    const i64 id = idx[0];
                     if (L.pop[id] < 0) neg ^= 1;
-                    Det<K> de = load_det<K>(L.bits, L.cap, id);
-                    if (!apply_excitor(s, de, dj, par)) valid = false;   // shared orbital
+                    dj = load_det<K>(L.bits, L.cap, id);
+                    par = excitor_sign(s, dj) < 0 ? 1 : 0;
+                } else {
+                    for (int e = 0; e < sz && valid; e++) {
+                        const i64 id = idx[e];
+                        if (L.pop[id] < 0) neg ^= 1;
+                        Det<K> de = load_det<K>(L.bits, L.cap, id);
+                        if (!apply_excitor(s, de, dj, par)) valid = false;   // shared orbital
+                    }
                 }
                 if (valid) {
                     if (n0 < 0 && ((sz - 1) & 1)) neg ^= 1;
@@ -699,8 +713,11 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
             int lev = valid ? level_of(s, dj) : 0;
             if (valid && lev <= s.lmax + 2) {
                 double coef = (par & 1) ? -amp : amp;
-                if (lev == 1 || lev == 2) es.add(to_fix(h_ref<K, R>(s, dj) * coef));
-                int sdj = excitor_sign(s, dj);
+                // a single excitor collapses to its own determinant: <HF|H|D> cached per entry
+                if (lev == 1 || lev == 2)
+                    es.add(to_fix((sz == 1 && !p.fnc ? wa.href[idx0] : h_ref<K, R>(s, dj)) * coef));
+                // s_D of the collapsed determinant (HF: +1; one excitor: known)
+                const int sdj = sz == 0 ? 1 : (sz == 1 ? ((par & 1) ? -1 : 1) : excitor_sign(s, dj));
                 if (sz <= 1) {
                     double x = wa.tdeath[idx0] * coef;   // tau (Delta E - S) C (idx0 = 0 for the reference)
                     if (sdj > 0) x = -x;
