@@ -923,9 +923,16 @@ __device__ __forceinline__ void d_sort_scatter(const u64 *kin, const i64 *vin, u
                                                                 const unsigned *hist, const unsigned *totals)
 {
     constexpr int NW = SORT_THREADS / 32;
+    static_assert((1 << MAX_DIGIT_BITS) <= SORT_THREADS, "one thread per digit in the tile scans");
     __shared__ unsigned s_off[1 << MAX_DIGIT_BITS];
     __shared__ unsigned s_tot[1 << MAX_DIGIT_BITS];
+    __shared__ unsigned s_tpre[1 << MAX_DIGIT_BITS];
     __shared__ unsigned s_w[NW][1 << MAX_DIGIT_BITS];
+    // the tile in digit order, so that each digit's run is written out by
+    // consecutive threads to consecutive addresses
+    __shared__ u64 s_tk[SORT_TILE];
+    __shared__ i64 s_tv[SORT_TILE];
+    __shared__ i64 s_sc[32];
     const int nd = 1 << bits;
     const u64 mask = (u64)nd - 1;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -982,13 +989,32 @@ __device__ __forceinline__ void d_sort_scatter(const u64 *kin, const i64 *vin, u
             s_tot[d] = run;
         }
         __syncthreads();
+        {
+            // exclusive prefix of the tile's digit counts (nd <= blockDim)
+            const int d = threadIdx.x;
+            const i64 v = d < nd ? (i64)s_tot[d] : 0;
+            i64 tot;
+            const i64 incl = block_incl_scan(v, s_sc, tot);
+            if (d < nd) s_tpre[d] = (unsigned)(incl - v);
+        }
+        __syncthreads();
+        // stable order within the tile: digit, then warp, then item, then lane
 #pragma unroll
         for (int j = 0; j < SORT_ITEMS; j++) {
             if (ok[j]) {
-                unsigned pos = s_off[dg[j]] + s_w[wid][dg[j]] + rk[j];
-                kout[pos] = kk[j];
-                vout[pos] = vv[j];
+                const unsigned tp = s_tpre[dg[j]] + s_w[wid][dg[j]] + rk[j];
+                s_tk[tp] = kk[j];
+                s_tv[tp] = vv[j];
             }
+        }
+        __syncthreads();
+        const int tn = (int)(hi - tb < (i64)SORT_TILE ? hi - tb : (i64)SORT_TILE);
+        for (int q = threadIdx.x; q < tn; q += blockDim.x) {
+            const u64 k = s_tk[q];
+            const unsigned d = (unsigned)((k >> shift) & mask);
+            const unsigned pos = s_off[d] + (unsigned)q - s_tpre[d];
+            kout[pos] = k;
+            vout[pos] = s_tv[q];
         }
         __syncthreads();
         for (int d = threadIdx.x; d < nd; d += blockDim.x) s_off[d] += s_tot[d];
