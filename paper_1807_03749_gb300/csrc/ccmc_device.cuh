@@ -352,23 +352,34 @@ __device__ __forceinline__ Det<K> unrank_key(const SysDev &s, u64 key)
     for (int w = 0; w < K; w++) d.w[w] = s.hf[w];
     u64 rv = (key + s.cocc - 1) / s.cocc;
     u64 rh = rv * s.cocc - key;
-    int c = 0;
-    for (int q = s.nso - s.nel - 1; q >= 0 && c <= s.lmax; q--) {
-        u64 cnt = __ldg(&s.rank_tab[c * RANK_STRIDE + q]);
-        if (rv >= cnt) {
-            rv -= cnt;
-            flip(d, q + s.nel);
-            c++;
+    // digit c of a rank: the largest position q below the previous digit with
+    // tab[c][q] <= rank (tab[c][q] grows with q; tab[c][0] = 1, so a zero
+    // rank has no further digits) -- a binary search per digit
+    int top = s.nso - s.nel;
+    for (int c = 0; c <= s.lmax && rv > 0 && top > 0; c++) {
+        const u64 *t = s.rank_tab + c * RANK_STRIDE;
+        int lo = 0, hi = top - 1;   // tab[c][0] = 1 <= rv
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&t[mid]) <= rv) lo = mid;
+            else hi = mid - 1;
         }
+        rv -= __ldg(&t[lo]);
+        flip(d, lo + s.nel);
+        top = lo;
     }
-    c = 0;
-    for (int q = s.nel - 1; q >= 0 && c <= s.lmax; q--) {
-        u64 cnt = __ldg(&s.rank_tab[c * RANK_STRIDE + q]);
-        if (rh >= cnt) {
-            rh -= cnt;
-            flip(d, q);
-            c++;
+    top = s.nel;
+    for (int c = 0; c <= s.lmax && rh > 0 && top > 0; c++) {
+        const u64 *t = s.rank_tab + c * RANK_STRIDE;
+        int lo = 0, hi = top - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&t[mid]) <= rh) lo = mid;
+            else hi = mid - 1;
         }
+        rh -= __ldg(&t[lo]);
+        flip(d, lo);
+        top = lo;
     }
     return d;
 }
