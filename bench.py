@@ -443,7 +443,9 @@ def run_gpu(args, w):
             ctx.set_state(STATE_ITER, STATE_SHIFT, 1, ntot0)
         h2d += bits.nbytes + pop.nbytes
         ctx.step(1)
-        out_bits, keys_h, out_pop = ctx.get_list(out=bufs[(k + 1) % 2])
+        # outputs alternate between the two buffers; with a restored start
+        # state the input stays in the first and every output goes to the second
+        out_bits, keys_h, out_pop = ctx.get_list(out=bufs[1] if restore is not None else bufs[(k + 1) % 2])
         en = ctx.energy()
         d2h += out_bits.nbytes + keys_h.nbytes + out_pop.nbytes + 40
         if restore is None:
