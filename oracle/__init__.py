@@ -7,7 +7,7 @@ generators in ``ccmc_inputs``.
 
 The arithmetic lives in ``ccmc_oracle.c`` (plain C, FP64, no fused
 multiply-add); this module compiles it with gcc and wraps it with ctypes.
-The brute-force checkers that pin the oracle live in ``oracle.brute``.
+The brute-force references that pin the oracle live in ``oracle.brute``.
 """
 from __future__ import annotations
 

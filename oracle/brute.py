@@ -1,4 +1,4 @@
-"""Brute-force checkers that pin the oracle (test infrastructure only).
+"""Brute-force references that pin the oracle (test infrastructure only).
 
 Nothing here calls the C oracle; these are independent, literal restatements
 of the textbook definitions the paper relies on, for tiny systems only:
