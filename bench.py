@@ -463,7 +463,7 @@ def run_gpu(args, w):
         fp32_energy = fp32_vs_fp64(ccmc, w, ctx, stream, start_list, start_state, min(args.steps, 200), rank)
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the oracle baseline is a 1-GPU figure
         cpu = cpu_baseline(w)
 
     if rank != 0:
