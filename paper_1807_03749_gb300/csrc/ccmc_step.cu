@@ -12,6 +12,10 @@
 //  a8  k_seg_*     : sum of each run of equal keys
 //  a9  k_merge_*   : merge into the list, occupation threshold, compaction
 //  a10 k_finalize  : projected-energy numerator, per-step record
+//  batch k_sample_plan / k_sample_flat: the sampler as one persistent launch
+//      over many replicas, with a work plan written on the device each step
+//  ccmc_reduce_records_noalloc (end of file): the sort and reduction as a
+//      standalone call on a static scratch array
 #include <mutex>
 
 #include "../../include/ccmc.h"
