@@ -1322,7 +1322,7 @@ ccmc_status ccmc_batch_create(ccmc_ctx **ctxs, int32_t n, void *cuda_stream, ccm
     ok = ok && cudaGetDevice(&dev) == cudaSuccess &&
          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
          cudaEventCreate(&b->tune_ev[0]) == cudaSuccess && cudaEventCreate(&b->tune_ev[1]) == cudaSuccess;
-    b->flat_grid = 3 * std::max(1, sms);   // resident blocks of the sampler (3 per SM)
+    b->flat_grid = 4 * std::max(1, sms);   // resident blocks of the sampler (4 per SM)
     for (int r = 0; r < n; r++) b->pop_now += ctxs[r]->prm.d0_init;
     b->tune_best = b->shape;
     b->tune_best_ms = 1e30f;

@@ -1326,7 +1326,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(const StepArgs *__r
 }
 
 template <int K, typename R>
-__global__ void __launch_bounds__(WORK_THREADS, 3) k_sample(const StepArgs *__restrict__ A, int enum_base)
+__global__ void __launch_bounds__(WORK_THREADS, 4) k_sample(const StepArgs *__restrict__ A, int enum_base)
 {
     REPLICA_SMEM;
     d_sample<K, R>(a.s, a.list[cur_], a.st, a.p, a.wa, a.sp, a.cl, enum_base, blockIdx.x, gridDim.x);
@@ -1379,7 +1379,7 @@ __global__ void __launch_bounds__(1024) k_sample_plan(const StepArgs *__restrict
 // Persistent batch sampler: each block takes the next virtual block of the
 // plan, finds its replica and runs that share of the replica's samples.
 template <int K, typename R>
-__global__ void __launch_bounds__(WORK_THREADS, 3) k_sample_flat(const StepArgs *__restrict__ A, int nrep, FlatPlan fp,
+__global__ void __launch_bounds__(WORK_THREADS, 4) k_sample_flat(const StepArgs *__restrict__ A, int nrep, FlatPlan fp,
                                                                  int enum_base)
 {
     __shared__ StepArgs a_sm;
