@@ -28,8 +28,9 @@
  *   - A "key" is the rank of a determinant among all determinants of
  *     excitation level <= l in that order (HF has key 0).
  *   - Every function returns a ccmc_status; nothing traps or aborts.  Errors
- *     found by kernels (buffer overflow, numeric overflow) are recorded in a
- *     device status word and reported by the next synchronising call.
+ *     found by kernels (buffer overflow, numeric overflow, a runaway
+ *     population) are recorded in a device status word and reported by the
+ *     next synchronising call.  No kernel waits on another.
  *   - One context per CUDA stream; calls on one context are not thread-safe.
  *   - Host pointers are read during the call only (the library copies what it
  *     keeps).  Device memory is owned by the context and released by ccmc_free.
@@ -177,8 +178,12 @@ ccmc_status ccmc_get_list(ccmc_ctx *ctx, uint64_t *bits, uint64_t *keys, int64_t
                           size_t *n);
 
 /* Replaces the excip list from host buffers (n determinants of K words and
- * their populations).  The list must be sorted, unique, start with HF and stay
- * within the truncation level; otherwise CCMC_ERR_ARG. */
+ * their populations).  The list must be sorted, unique, start with HF, stay
+ * within the truncation level and within the reference's sector (its S_z,
+ * and for the gas its total momentum: the sector every spawn stays in);
+ * otherwise CCMC_ERR_ARG and the context keeps its previous list.  The checks
+ * run on the device; the list is uploaded into the context's spare list
+ * buffer, which becomes current only if it passes. */
 ccmc_status ccmc_set_list(ccmc_ctx *ctx, const uint64_t *bits, const int64_t *pop, size_t n);
 
 /* The spawned records of the latest step (keys and fixed-point weights,
