@@ -43,3 +43,13 @@ def test_read_traffic_from_profiles():
     b, issue = bench.read_traffic("ueg14_m114_ccsdt_fnc_ms", "attempts")
     assert b is not None and b > 0 and 0 < issue <= 100
     assert bench.read_traffic("no_such_workload", "sample") == (None, None)
+
+
+def test_oracle_on_several_cores_small_workload():
+    """The CPU baseline's process pool (spawned processes, a barrier, slices
+    of one full step) on the 38 spin-orbital gas with two processes."""
+    from ccmc_inputs import workload
+
+    w = workload("ueg14_m38_ccsd")
+    v, kps, cores, secs, nslices = bench.oracle_all_cores(w, 0, 2, cores=2, per_slice=2000)
+    assert cores == 2 and v > 0 and secs > 0 and nslices >= 1 and kps >= 0
