@@ -248,7 +248,10 @@ typedef struct ccmc_batch ccmc_batch;
 
 /* Groups n contexts (which must all use the same shift_a) into a batch whose
  * work is issued on cuda_stream (must not be NULL).  The contexts stay owned
- * by the caller and must not be stepped on their own while in the batch. */
+ * by the caller; while in the batch, ccmc_step on them returns
+ * CCMC_ERR_STATE (reading, ccmc_set_list and checkpoints remain allowed), and
+ * a context in another batch is rejected with CCMC_ERR_STATE.  Free the
+ * batch before its contexts. */
 ccmc_status ccmc_batch_create(ccmc_ctx **ctxs, int32_t n, void *cuda_stream, ccmc_batch **out);
 
 /* nsteps steps of every context in the batch.  The host synchronises at each

@@ -221,6 +221,8 @@ struct ccmc_ctx {
     // the validation word of the last upload
     u64 *io = nullptr;
     unsigned *d_bad = nullptr, *h_bad = nullptr;
+    // the batch that steps this context, if any (it is not stepped alone then)
+    ccmc_batch *batch = nullptr;
 };
 
 namespace {
@@ -772,6 +774,7 @@ static cudaError_t issue_step(ccmc_ctx *ctx)
 ccmc_status ccmc_step(ccmc_ctx *ctx, int nsteps)
 {
     if (!ctx || nsteps < 0) return CCMC_ERR_ARG;
+    if (ctx->batch) return fail(ctx, CCMC_ERR_STATE, "the context is stepped by its batch");
     const int A = ctx->prm.shift_a;
     for (int k = 0; k < nsteps; k++) {
         cudaError_t e = issue_step(ctx);
@@ -1254,6 +1257,7 @@ ccmc_status ccmc_batch_create(ccmc_ctx **ctxs, int32_t n, void *cuda_stream, ccm
     if (!ctxs || n < 1 || !cuda_stream) return CCMC_ERR_ARG;
     for (int r = 0; r < n; r++) {
         if (!ctxs[r] || ctxs[r]->prm.shift_a != ctxs[0]->prm.shift_a) return CCMC_ERR_ARG;
+        if (ctxs[r]->batch) return CCMC_ERR_STATE;   // already in a batch
         for (int q = 0; q < r; q++)
             if (ctxs[q] == ctxs[r]) return CCMC_ERR_ARG;
     }
@@ -1330,6 +1334,7 @@ ccmc_status ccmc_batch_create(ccmc_ctx **ctxs, int32_t n, void *cuda_stream, ccm
         ccmc_batch_free(b);
         return CCMC_ERR_OOM;
     }
+    for (ccmc_ctx *c : b->ctxs) c->batch = b;
     *out = b;
     return CCMC_OK;
 }
@@ -1477,6 +1482,8 @@ ccmc_status ccmc_batch_info(ccmc_batch *b, int32_t *work_blocks, int32_t *sample
 void ccmc_batch_free(ccmc_batch *b)
 {
     if (!b) return;
+    for (ccmc_ctx *c : b->ctxs)
+        if (c && c->batch == b) c->batch = nullptr;
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     for (cudaEvent_t e : b->events) cudaEventDestroy(e);

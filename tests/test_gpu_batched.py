@@ -45,3 +45,27 @@ def test_batched_equals_plain(ccmc_lib=None):
     info = b.info()
     assert info["groups"] == 3 and info["work_blocks"] in (32, 64, 128, 256) and info["digit_bits"] in (6, 8)
     assert info["sample_tile"] in (256, 512, 1024, 2048, 4096) and info["tunings"] >= 1
+
+
+def test_batch_members_are_not_stepped_alone():
+    """While a context belongs to a batch, stepping it alone is refused (the
+    batch owns its step sequence) and it cannot join a second batch; after
+    the batch is released it steps normally."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA")
+    import paper_1807_03749_gb300 as ccmc
+
+    stream = torch.cuda.Stream()
+    w = workload("ueg14_m38_ccsd")
+    a, c = ccmc.from_workload(w), ccmc.from_workload(w, replica=1)
+    b = ccmc.Batch([a, c], stream.cuda_stream)
+    b.step(3)
+    with pytest.raises(ccmc.CCMCError) as e:
+        a.step(1)
+    assert e.value.status == 8
+    with pytest.raises(ccmc.CCMCError):
+        ccmc.Batch([a], stream.cuda_stream)
+    b.close()
+    a.step(2)
+    assert a.get_state()[0] == 5
