@@ -249,9 +249,14 @@ typedef struct ccmc_batch ccmc_batch;
 /* Groups n contexts (which must all use the same shift_a) into a batch whose
  * work is issued on cuda_stream (must not be NULL).  The contexts stay owned
  * by the caller; while in the batch, ccmc_step on them returns
- * CCMC_ERR_STATE (reading, ccmc_set_list and checkpoints remain allowed), and
- * a context in another batch is rejected with CCMC_ERR_STATE.  Free the
- * batch before its contexts. */
+ * CCMC_ERR_STATE, and a context in another batch is rejected with
+ * CCMC_ERR_STATE.  Reading a member (lists, records, energies, spawned
+ * records, death deltas), ccmc_set_list, ccmc_set_state and checkpoints
+ * remain allowed: each such call first waits for the batch's stream, so it
+ * sees (or replaces) the state after the batch's last issued step.  Free the
+ * batch before its contexts; a member freed first is detached from the batch
+ * (after waiting for the batch's stream), and the batch then refuses to step
+ * (CCMC_ERR_STATE) and can only be freed. */
 ccmc_status ccmc_batch_create(ccmc_ctx **ctxs, int32_t n, void *cuda_stream, ccmc_batch **out);
 
 /* nsteps steps of every context in the batch.  The host synchronises at each
@@ -279,23 +284,30 @@ void ccmc_batch_free(ccmc_batch *b);
 
 /* Sorts n spawned records by key and sums each run of equal keys -- the
  * annihilation's sort and reduction as a standalone call -- without
- * allocating anything.  The paper has no counterpart: it is for callers that
- * cannot call cudaMalloc (code issued inside CUDA graph capture, real-time
- * loops with a fixed memory budget, hosts that own the device allocator).
+ * allocating any device memory.  The paper has no counterpart.  It is for
+ * callers that may not call cudaMalloc or an allocating library routine:
+ * plugins whose host application owns the device allocator, and loops that
+ * must keep a fixed device-memory footprint once set up.
  *   keys_in, pops_in   device arrays of n records (read only)
- *   key_bits           significant bits of the keys (1..64)
+ *   key_bits           significant bits of the keys (1..64); keys with bits
+ *                      set above key_bits are outside the contract and are
+ *                      not sorted correctly
  *   keys_out, pops_out device arrays with room for n records; receive the
  *                      distinct keys in increasing order and their summed
  *                      weights (runs that sum to zero are kept)
  *   n_out              host pointer; receives the number of distinct keys
  *   cuda_stream        cudaStream_t for the work (NULL = legacy stream); the
  *                      call waits for it before returning
- * Scratch is one fixed 2 MiB device array inside the library, held by every
- * GPU that loads it until the process exits; n above
- * CCMC_NOALLOC_MAX_RECORDS is rejected with CCMC_ERR_ARG.  The first call on
- * a device looks up that array's device address (once per device); make that
- * first call before any stream capture.  All calls share the array, so calls
- * that overlap on the GPU (other streams, other threads) race and must be
+ * Scratch is one fixed device array inside the library of about 2.07 MiB
+ * (two ping-pong buffers of CCMC_NOALLOC_MAX_RECORDS keys and weights, 2 MiB,
+ * plus histograms, block partials and counters), held by every GPU that
+ * loads the library until the process exits.  n above
+ * CCMC_NOALLOC_MAX_RECORDS is rejected with CCMC_ERR_ARG before any work.
+ * The first call on a device looks up that array's device address (once per
+ * device, with the device current); make that first call before any stream
+ * capture.  The array is shared per device by every caller in the process
+ * (other streams, other threads, other library contexts) and keeps the last
+ * call's contents; calls that overlap on the GPU race and must be
  * serialised by the caller. */
 ccmc_status ccmc_reduce_records_noalloc(const uint64_t *keys_in, const int64_t *pops_in, size_t n, int32_t key_bits,
                                         uint64_t *keys_out, int64_t *pops_out, size_t *n_out, void *cuda_stream);

@@ -221,9 +221,14 @@ struct ccmc_ctx {
     // the validation word of the last upload
     u64 *io = nullptr;
     unsigned *d_bad = nullptr, *h_bad = nullptr;
-    // the batch that steps this context, if any (it is not stepped alone then)
+    // the batch that steps this context, if any (it is not stepped alone
+    // then), and the stream its batched steps run on
     ccmc_batch *batch = nullptr;
+    cudaStream_t batch_stream = nullptr;
 };
+
+// Removes a context that is being freed from its batch (defined with the batch).
+static void batch_detach(ccmc_batch *b, ccmc_ctx *c);
 
 namespace {
 
@@ -243,6 +248,13 @@ ccmc_status cuda_fail(ccmc_ctx *c, cudaError_t e, const char *where)
         cudaError_t e_ = (call);                                   \
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
     } while (0)
+
+// A batch member's device state is written by the batch's graph on the
+// batch's stream: every call that reads or writes that state waits for it.
+cudaError_t wait_batch(ccmc_ctx *ctx)
+{
+    return ctx->batch ? cudaStreamSynchronize(ctx->batch_stream) : cudaSuccess;
+}
 
 ccmc_status status_from_bits(ccmc_ctx *ctx, unsigned bits)
 {
@@ -701,6 +713,7 @@ ccmc_status ccmc_set_list(ccmc_ctx *ctx, const uint64_t *bits, const int64_t *po
     // every spawn stays in, so a gas list has no single excitations --,
     // truncation level, HF first, strictly increasing keys.  The upload goes
     // to the spare list buffer, which becomes current only if it passes.
+    CK(wait_batch(ctx));
     const int nb = ctx->sc.cur ^ 1;
     ListView &L = ctx->sc.list[nb];
     CK(cudaMemsetAsync(ctx->d_bad, 0, sizeof(unsigned), ctx->stream));
@@ -731,6 +744,7 @@ ccmc_status ccmc_set_list(ccmc_ctx *ctx, const uint64_t *bits, const int64_t *po
 
 static ccmc_status check_device(ccmc_ctx *ctx)
 {
+    CK(wait_batch(ctx));
     CK(cudaMemcpyAsync(ctx->h_st, ctx->sc.st, sizeof(DevStep), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return status_from_bits(ctx, ctx->h_st->err);
@@ -814,6 +828,7 @@ ccmc_status ccmc_step(ccmc_ctx *ctx, int nsteps)
 ccmc_status ccmc_profile(ccmc_ctx *ctx, int32_t enable)
 {
     if (!ctx) return CCMC_ERR_ARG;
+    CK(wait_batch(ctx));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->sc.profile = enable != 0;
     for (int ph = 0; ph < 8; ph++) {
@@ -944,6 +959,7 @@ ccmc_status ccmc_get_spawned(ccmc_ctx *ctx, uint64_t *keys, int64_t *pop, size_t
 ccmc_status ccmc_get_death(ccmc_ctx *ctx, int64_t *death, size_t cap, size_t *n)
 {
     if (!ctx || !n) return CCMC_ERR_ARG;
+    CK(wait_batch(ctx));
     CK(cudaStreamSynchronize(ctx->stream));
     if (!ctx->stepped) {
         *n = 0;
@@ -966,6 +982,7 @@ ccmc_status ccmc_set_state(ccmc_ctx *ctx, uint64_t iter, double shift, int32_t v
     ctx->vary = vary ? 1 : 0;
     ctx->nprev = nprev;
     ctx->records_read = iter;
+    CK(wait_batch(ctx));
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaMemcpy(&ctx->sc.st->iter, &iter, sizeof(u64), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(&ctx->sc.st->shift, &shift, sizeof(double), cudaMemcpyHostToDevice));
@@ -1044,6 +1061,7 @@ const char *ccmc_last_error(ccmc_ctx *ctx)
 void ccmc_free(ccmc_ctx *ctx)
 {
     if (!ctx) return;
+    if (ctx->batch) batch_detach(ctx->batch, ctx);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
@@ -1112,6 +1130,7 @@ int tune_count(int stage)
 struct ccmc_batch {
     std::vector<ccmc_ctx *> ctxs;
     cudaStream_t stream = nullptr;
+    bool member_freed = false;        // a member context was freed: the batch can no longer step
     std::vector<BatchGroup> groups;
     StepArgs *d_all = nullptr;       // every replica, for gather / shift scatter
     Record *d_rec = nullptr, *h_rec = nullptr;
@@ -1137,6 +1156,19 @@ struct ccmc_batch {
     double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     i64 launch0[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
+
+// A member freed while in the batch: wait for the batch's work, drop the
+// member's slot and refuse further batched steps (the captured graph and
+// the per-replica argument arrays still point at the member's memory).
+static void batch_detach(ccmc_batch *b, ccmc_ctx *c)
+{
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (ccmc_ctx *&m : b->ctxs)
+        if (m == c) m = nullptr;
+    b->member_freed = true;
+    c->batch = nullptr;
+    c->batch_stream = nullptr;
+}
 
 namespace {
 
@@ -1334,7 +1366,10 @@ ccmc_status ccmc_batch_create(ccmc_ctx **ctxs, int32_t n, void *cuda_stream, ccm
         ccmc_batch_free(b);
         return CCMC_ERR_OOM;
     }
-    for (ccmc_ctx *c : b->ctxs) c->batch = b;
+    for (ccmc_ctx *c : b->ctxs) {
+        c->batch = b;
+        c->batch_stream = b->stream;
+    }
     *out = b;
     return CCMC_OK;
 }
@@ -1412,6 +1447,7 @@ static ccmc_status batch_capture(ccmc_batch *b)
 ccmc_status ccmc_step_batched(ccmc_batch *b, int32_t nsteps)
 {
     if (!b || nsteps < 0) return CCMC_ERR_ARG;
+    if (b->member_freed) return CCMC_ERR_STATE;
     for (int k = 0; k < nsteps; k++) {
         Shapes launched = b->sh;
         if (!b->tuned) {
@@ -1482,9 +1518,12 @@ ccmc_status ccmc_batch_info(ccmc_batch *b, int32_t *work_blocks, int32_t *sample
 void ccmc_batch_free(ccmc_batch *b)
 {
     if (!b) return;
-    for (ccmc_ctx *c : b->ctxs)
-        if (c && c->batch == b) c->batch = nullptr;
     if (b->stream) cudaStreamSynchronize(b->stream);
+    for (ccmc_ctx *c : b->ctxs)
+        if (c && c->batch == b) {
+            c->batch = nullptr;
+            c->batch_stream = nullptr;
+        }
     if (b->graph) cudaGraphExecDestroy(b->graph);
     for (cudaEvent_t e : b->events) cudaEventDestroy(e);
     for (cudaEvent_t e : b->tune_ev)

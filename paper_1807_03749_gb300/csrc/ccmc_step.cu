@@ -1659,11 +1659,13 @@ cudaError_t launch_step(StepCtx &c)
 // ---------------------------------------------------------------------------
 // Sort-and-reduce of spawned records without any allocation
 //
-// For callers that cannot allocate device memory themselves: code running
-// inside a captured CUDA graph or a pre-sized real-time loop, plugins whose
-// host owns the device allocator, or tools that must not grow the memory
-// footprint.  The scratch lives in one file-scope device array that every
-// GPU loading this library holds until the process exits.
+// For callers that may not allocate device memory: plugins whose host
+// application owns the device allocator, and loops that must keep a fixed
+// device-memory footprint once set up.  The scratch lives in one file-scope
+// device array that every GPU loading this library holds until the process
+// exits; every call on a device shares it and leaves its contents behind
+// (the counters the kernels rely on are reset by k_noalloc_begin and the
+// output weights are zeroed before the per-run atomics).
 // ---------------------------------------------------------------------------
 
 namespace ccmc {

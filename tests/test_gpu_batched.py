@@ -69,3 +69,55 @@ def test_batch_members_are_not_stepped_alone():
     b.close()
     a.step(2)
     assert a.get_state()[0] == 5
+
+
+def test_batch_member_freed_before_the_batch():
+    """Freeing a member context first detaches it: the batch then refuses to
+    step (its graph still points at the freed memory) and can be freed; the
+    other member stays usable."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA")
+    import paper_1807_03749_gb300 as ccmc
+
+    stream = torch.cuda.Stream()
+    w = workload("ueg14_m38_ccsd")
+    a, c = ccmc.from_workload(w), ccmc.from_workload(w, replica=1)
+    b = ccmc.Batch([a, c], stream.cuda_stream)
+    b.step(3)
+    a.close()
+    with pytest.raises(ccmc.CCMCError) as e:
+        b.step(1)
+    assert e.value.status == 8
+    b.close()
+    c.step(2)
+    assert c.get_state()[0] == 5
+
+
+def test_member_reads_wait_for_the_batch_stream():
+    """Reads of a member right after ccmc_step_batched (work still pending on
+    the batch's stream, no shift boundary reached) see the state after the
+    issued steps: the same list as after an explicit synchronisation and as
+    the same context stepped alone."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA")
+    import paper_1807_03749_gb300 as ccmc
+
+    stream = torch.cuda.Stream()
+    w = workload("ueg14_m114_ccsdt_fnc_ms", target_pop=2e4)
+    a = ccmc.from_workload(w)
+    ref = ccmc.from_workload(w)
+    b = ccmc.Batch([a], stream.cuda_stream)
+    b.step(40)      # tuning and growth, ends on a shift boundary
+    ref.step(40)
+    b.step(3)       # no boundary: returns with the steps in flight
+    ref.step(3)
+    early = a.get_list()
+    torch.cuda.synchronize()
+    late = a.get_list()
+    want = ref.get_list()
+    for x, y, z in zip(early, late, want):
+        assert np.array_equal(x, y) and np.array_equal(x, z)
+    assert a.records()[-1] == ref.records()[-1]
+    b.close()
