@@ -33,11 +33,23 @@ WORKLOADS = {
     "ueg14_m114_ccsdt_fnc_ms": dict(kind="ueg", nel=14, nso=114, rs=1.0, lmax=3, target_pop=1.0e6,
                                     tau=0.005, nsteps=2000, seed=1, fnc=True, multispawn=True),
     # synthetic molecule: 20 e in 41 spatial orbitals (82 spin-orbitals), CCSDTQ.
-    # With these integrals no population grown from the reference settles
-    # (every run tried ran away within 600 steps), so each timed step starts
-    # from the same synthetic full-size state (molecule_state).
+    # With these integrals (N(0,1) magnitudes) the spawned weight per step
+    # is about tau * 2.5e3 E_h times the population, and the shift, updated
+    # every shift_a steps with damping zeta, holds the population only when
+    # shift_a * tau * 2.5e3 is well below zeta: tau = 2e-6.  Every population
+    # reachable on one GPU is then below the annihilation plateau, so the
+    # wavefunction is noise-dominated; the reference starts with 2e6
+    # particles so that it keeps a sizeable share through the timed window.
+    # (molecule_state gives a separate full-size synthetic list for parity
+    # tests of single steps.)
     "mol20_m82_ccsdtq": dict(kind="generic", nel=20, norb=41, lmax=4, target_pop=1.0e7,
-                             tau=0.005, nsteps=50, seed=1, molecule_seed=7, from_state=True, state_seed=31),
+                             tau=2.0e-6, nsteps=50, seed=1, molecule_seed=7, d0_init=2.0e6,
+                             equilibrate=400, list_capacity=40_000_000, state_seed=31),
+    # UEG 14 e / 358 spin-orbitals (179 plane waves, |n|^2 <= 12; six-word
+    # determinants), r_s = 1, CCSDTQ: the system of the paper's published
+    # correlation energy (Sec. III.B), full non-composite + multi-spawn.
+    "ueg14_m358_ccsdtq": dict(kind="ueg", nel=14, nso=358, rs=1.0, lmax=4, target_pop=3.0e7,
+                              tau=0.003, nsteps=20000, seed=1, fnc=True, multispawn=True, d0_init=1.0e4),
     # UEG 54 e / 162 spin-orbitals (81 plane waves), CCSD, FP32 matrix elements.
     # 10^4 initial particles on HF: from 100 the original sampler stays below
     # the shoulder on this system and the population blows up.  Grown at 1% of

@@ -21,7 +21,8 @@
  * Conventions
  *   - Spin-orbital p is bit (p & 63) of word (p >> 6) of a determinant;
  *     spin-orbital 2q is alpha and 2q+1 beta of spatial orbital q.  A
- *     determinant with M spin-orbitals uses K = ceil(M/64) words (M <= 192).
+ *     determinant with M spin-orbitals uses K = ceil(M/64) words (M <= 384;
+ *     the FP32 form M <= 192).
  *   - Determinants are ordered as unsigned integers compared from the most
  *     significant word; the Hartree-Fock (HF) reference is the lowest N bits.
  *   - Populations are int64 fixed point: value = pop / 2^16.
@@ -75,7 +76,7 @@ enum { CCMC_FP64 = 0, CCMC_FP32 = 1 };
 typedef struct {
     int32_t kind;
     int32_t n_electrons;   /* N */
-    int32_t n_spinorb;     /* M, even, N < M <= 192 */
+    int32_t n_spinorb;     /* M, even, N < M <= 384 (FP32 form: <= 192) */
     int32_t reserved;
     double rs;             /* UEG density parameter (bohr) */
     const double *h1;      /* GENERIC only */
@@ -114,12 +115,21 @@ typedef struct {
     ccmc_free_fn free;
     void *alloc_user;
     int32_t radix_bits;      /* digit width of the radix sort, 0 = default */
-    int32_t flags;           /* CCMC_NO_GRAPH: launch kernels one by one instead of
-                                replaying a captured CUDA graph of the step */
+    int32_t flags;           /* CCMC_NO_GRAPH, CCMC_SORT_ALL (below) */
 } ccmc_params;
 
-/* ccmc_params.flags */
+/* ccmc_params.flags
+ *   CCMC_NO_GRAPH  launch the step's kernels one by one instead of replaying a
+ *                  captured CUDA graph of the step.
+ *   CCMC_SORT_ALL  send every spawned record through the radix sort.  By
+ *                  default a record whose determinant is already in the excip
+ *                  list is added to that entry directly (an integer atomic)
+ *                  and only records onto new determinants are sorted; the
+ *                  merged list is identical either way (integer sums), but
+ *                  ccmc_get_spawned then returns the sorted records onto new
+ *                  determinants only.  With this flag it returns all of them. */
 #define CCMC_NO_GRAPH 1
+#define CCMC_SORT_ALL 2
 
 /* Per-step record; one is kept for every step in a device ring buffer. */
 typedef struct {
@@ -135,6 +145,9 @@ typedef struct {
     int64_t ntot_after;   /* N_total after annihilation */
     int64_t nocc_after;   /* occupied excitors after annihilation */
     int64_t n_keys;       /* distinct keys among the spawned records */
+    int64_t n_clusters;   /* composite clusters buffered for multi-spawn attempts */
+    int64_t n_direct;     /* spawned records added directly to listed determinants
+                             (included in n_spawned; not sorted) */
 } ccmc_record;
 
 /* Creates a context: copies the Hamiltonian, builds orbital and matrix-element
@@ -186,9 +199,10 @@ ccmc_status ccmc_get_list(ccmc_ctx *ctx, uint64_t *bits, uint64_t *keys, int64_t
  * buffer, which becomes current only if it passes. */
 ccmc_status ccmc_set_list(ccmc_ctx *ctx, const uint64_t *bits, const int64_t *pop, size_t n);
 
-/* The spawned records of the latest step (keys and fixed-point weights,
- * sorted by key; composite deaths included) -- the multiset entering the
- * annihilation. */
+/* The spawned records of the latest step that went through the sort (keys
+ * and fixed-point weights, sorted by key; composite deaths included): with
+ * CCMC_SORT_ALL the whole multiset entering the annihilation, otherwise the
+ * records onto determinants not in the list at the start of the step. */
 ccmc_status ccmc_get_spawned(ccmc_ctx *ctx, uint64_t *keys, int64_t *pop, size_t cap, size_t *n);
 
 /* The death deltas of the latest step for the list entries of that step's

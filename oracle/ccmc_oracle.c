@@ -37,7 +37,8 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define OW 3                 /* maximum words per bit string (M <= 192) */
+#define OW 6                 /* maximum words per bit string (M <= 384) */
+#define OBINOM 385           /* binomial table rows C(n, k), n <= 384 */
 #define FIX_ONE 65536.0      /* populations are multiples of 2^-16 */
 #define FIX_SHIFT 16
 #define ORC_PI 3.14159265358979323846
@@ -162,7 +163,7 @@ typedef struct {
     /* common */
     double ehf_rel;      /* <HF|H|HF> without the constant ecore */
     double *fock;        /* F_p = h_pp + sum_{k in HF, k != p} <pk||pk>, per spin-orbital */
-    uint64_t binom[200][8];
+    uint64_t binom[OBINOM][8];
     uint64_t cocc;       /* number of hole sets with <= l holes */
     uint64_t nvranks;    /* number of particle sets with <= l particles */
     /* excitation generator constants */
@@ -185,7 +186,7 @@ static int spat_of(int p) { return p >> 1; }
 
 static void fill_binom(orc_system *s)
 {
-    for (int n = 0; n < 200; n++)
+    for (int n = 0; n < OBINOM; n++)
         for (int k = 0; k < 8; k++) {
             if (k == 0) s->binom[n][k] = 1;
             else if (n == 0) s->binom[n][k] = 0;

@@ -49,7 +49,8 @@ class Params(ctypes.Structure):
 class Record(ctypes.Structure):
     _fields_ = [("iter", c_uint64), ("shift", c_double), ("n0", c_int64), ("ntot", c_int64), ("n_sel", c_int64),
                 ("n_visit", c_int64), ("n_attempts", c_int64), ("n_spawned", c_int64), ("e_num", c_double),
-                ("ntot_after", c_int64), ("nocc_after", c_int64), ("n_keys", c_int64)]
+                ("ntot_after", c_int64), ("nocc_after", c_int64), ("n_keys", c_int64), ("n_clusters", c_int64),
+                ("n_direct", c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -148,7 +149,8 @@ class Context:
                  shift_a: int = 10, zeta: float = 0.05, spawn_cutoff: float = 2.0 ** -7, fnc: bool = False,
                  multispawn: bool = False, a_thresh: float = 1.0, seed: int = 1, replica: int = 0,
                  precision: str = "fp64", list_capacity: int = 0, spawn_capacity: int = 0, stream=None,
-                 use_torch_allocator: bool = False, radix_bits: int = 0, use_graph: bool = True, **_ignored):
+                 use_torch_allocator: bool = False, radix_bits: int = 0, use_graph: bool = True,
+                 sort_all: bool = False, **_ignored):
         L = load()
         self._lib = L
         self.nel, self.nso, self.lmax = nel, nso, lmax
@@ -174,7 +176,7 @@ class Context:
         p.seed, p.replica = seed, replica
         p.list_capacity, p.spawn_capacity = list_capacity, spawn_capacity
         p.radix_bits = radix_bits
-        p.flags = 0 if use_graph else 1
+        p.flags = (0 if use_graph else 1) | (2 if sort_all else 0)
         if stream is not None:
             p.cuda_stream = c_void_p(int(stream))
         if use_torch_allocator:

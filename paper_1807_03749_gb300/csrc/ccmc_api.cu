@@ -394,6 +394,7 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     if (params->multispawn && !(params->a_thresh > 0.0)) return CCMC_ERR_ARG;
     if (params->radix_bits < 0 || params->radix_bits > MAX_DIGIT_BITS) return CCMC_ERR_ARG;
     if (params->precision != CCMC_FP64 && params->precision != CCMC_FP32) return CCMC_ERR_ARG;
+    if (params->precision == CCMC_FP32 && nso > 192) return CCMC_ERR_ARG;   // FP32 form: up to three words
 
     ccmc_ctx *ctx = new (std::nothrow) ccmc_ctx();
     if (!ctx) return CCMC_ERR_OOM;
@@ -560,6 +561,7 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     rp.fnc = params->fnc ? 1 : 0;
     rp.multispawn = params->multispawn ? 1 : 0;
     rp.a_thresh_one = params->a_thresh == 1.0 ? 1 : 0;
+    rp.direct = (params->flags & CCMC_SORT_ALL) ? 0 : 1;
     {
         // work per step beyond which a runaway population is reported
         // instead of sampled: 64x the target, at least 2^24, at most 2^36
@@ -633,6 +635,10 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     wa.catt = al.arr<double>(lc);
     wa.death = al.arr<i64>(lc);
     wa.acc = al.arr<i64>(lc);
+    wa.kbucket_bits = 10;
+    while (wa.kbucket_bits < 25 && (1LL << wa.kbucket_bits) < 2 * lc) wa.kbucket_bits++;
+    wa.kbucket = al.arr<int>((size_t)1 << wa.kbucket_bits);
+    wa.hit = al.arr<unsigned char>(lc);
     wa.newpop = al.arr<i64>(lc);
     wa.keep_l = al.arr<i64>(lc);
     wa.keep_s = al.arr<i64>(sp.cap);
@@ -1358,7 +1364,7 @@ ccmc_status ccmc_batch_create(ccmc_ctx **ctxs, int32_t n, void *cuda_stream, ccm
     ok = ok && cudaGetDevice(&dev) == cudaSuccess &&
          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
          cudaEventCreate(&b->tune_ev[0]) == cudaSuccess && cudaEventCreate(&b->tune_ev[1]) == cudaSuccess;
-    b->flat_grid = 4 * std::max(1, sms);   // resident blocks of the sampler (4 per SM)
+    b->flat_grid = SAMPLE_BLOCKS_PER_SM * std::max(1, sms);   // resident blocks of the persistent sampler
     for (int r = 0; r < n; r++) b->pop_now += ctxs[r]->prm.d0_init;
     b->tune_best = b->shape;
     b->tune_best_ms = 1e30f;

@@ -18,8 +18,8 @@ namespace ccmc {
 typedef unsigned long long u64;
 typedef long long i64;
 
-constexpr int MAXK = 3;            // words per determinant (M <= 192)
-constexpr int RANK_STRIDE = 200;   // row stride of the rank tables
+constexpr int MAXK = 6;            // words per determinant (M <= 384)
+constexpr int RANK_STRIDE = 384;   // row stride of the rank tables (positions < M)
 constexpr double FIX_ONE = 65536.0;
 
 // Philox counter tags (bits 56..63 of counter word 1).

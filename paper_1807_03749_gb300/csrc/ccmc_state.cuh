@@ -14,6 +14,11 @@ constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 8;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
 constexpr int MAX_DIGIT_BITS = 8;
+// resident blocks of the cluster sampler per SM (its register budget)
+#ifndef CCMC_SAMPLE_BLOCKS_PER_SM
+#define CCMC_SAMPLE_BLOCKS_PER_SM 4
+#endif
+constexpr int SAMPLE_BLOCKS_PER_SM = CCMC_SAMPLE_BLOCKS_PER_SM;
 constexpr int RING = 1 << 14;             // per-step records kept on the device
 constexpr int CL_SHIFT = 38;              // packed (clusters << 38) | attempts
 constexpr u64 CL_MASK = (1ULL << CL_SHIFT) - 1ULL;
@@ -27,6 +32,7 @@ struct RunParams {
     int fnc, multispawn;
     int int_round;        // rounding decisions from the FP64 bit pattern (cutoff 0 or 2^k)
     int a_thresh_one;     // A_thresh == 1: floor(|A|) without a division
+    int direct;           // spawns onto listed determinants are added to them directly (not sorted)
     i64 work_cap;         // samples, visit attempts or cluster attempts per step beyond which the step is abandoned
     RoundSpec spawn_rs;   // spawn rounding (with the cutoff)
     RoundSpec death_rs;   // death rounding (no cutoff)
@@ -48,6 +54,8 @@ struct Record {
     i64 n0, ntot, n_sel, n_visit, n_attempts, n_spawned;
     double e_num;
     i64 ntot_after, nocc_after, n_keys;
+    i64 n_clusters;
+    i64 n_direct;
 };
 
 // Mutable per-step scalars living in device memory.
@@ -72,6 +80,11 @@ struct DevStep {
     double cl_att;      // attempts of the buffered clusters (runaway check; exact below 2^53)
     unsigned err;
     int cur;            // list buffer holding the current list
+    int kshift;         // key buckets cover 2^kshift keys each
+    int pad1;
+    i64 nkb;            // key buckets in use (0: no direct accumulation this step)
+    i64 n_direct;       // spawned records added directly to listed determinants
+    i64 n_hit;          // listed determinants that received such records
 };
 
 // Spawn buffer pair for the radix sort (ping-pong).
@@ -100,7 +113,10 @@ struct WorkArrays {
     i64 *att_end;     // inclusive prefix of full non-composite attempts
     double *catt;     // attempt coefficient of each list entry
     i64 *death;       // death deltas (fixed point)
-    i64 *acc;         // reduced spawned weight matched to each list entry
+    i64 *acc;         // spawned weight matched to each list entry (direct and reduced)
+    int *kbucket;     // first list entry of each key bucket (key >> kshift)
+    int kbucket_bits; // log2 of the key-bucket capacity
+    unsigned char *hit;  // list entries that received directly added spawns this step
     i64 *part;        // block partials of the scans (4 per block)
     u64 *enum_part;   // 128-bit fixed-point E_num partial (lo, hi) per producing block
     i64 *newpop;      // list values after the merge (threshold applied)

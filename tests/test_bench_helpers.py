@@ -24,25 +24,63 @@ def test_blocked_error_iid_and_correlated():
     assert bench.blocked_error(np.ones(5)) == 0.0                # too short for 8 blocks
 
 
+def test_mean_cluster_size_closed_forms():
+    # original sampler, l = 2: sum_s s p(s) = 1/4 + 2/8 + 3/16 + 4/16
+    assert bench.mean_cluster_size(2, False) == 0.25 + 0.25 + 0.1875 + 0.25
+    # full non-composite composites, l = 3: s = 2..5 with 1/2, 1/4, 1/8, 1/8
+    assert bench.mean_cluster_size(3, True) == 2 * 0.5 + 3 * 0.25 + 4 * 0.125 + 5 * 0.125
+    # the size distributions themselves sum to one
+    for l in (1, 2, 3, 4):
+        assert sum(2.0 ** -(s + 1) for s in range(l + 2)) + 2.0 ** -(l + 2) == 1.0
+        assert sum(2.0 ** -(s - 1) for s in range(2, l + 2)) + 2.0 ** -l == 1.0
+
+
 def test_algorithmic_bytes_per_phase():
-    r = dict(n_visit=0, nocc_after=1000, n_spawned=300, n_sel=2000, n_attempts=5000, n_keys=200)
+    r = dict(n_visit=0, nocc_after=1000, n_spawned=300, n_sel=2000, n_attempts=5000, n_keys=200, n_clusters=0)
     nw = 2
     be = 8 * nw + 16
-    assert bench.algorithmic_bytes("scan", [r], nw) == 1000 * 16
-    assert bench.algorithmic_bytes("sample", [r], nw) == 2000 * 0.97 * be + 300 * 16
-    assert bench.algorithmic_bytes("attempts", [r], nw) == 5000 * be + 300 * 16
-    assert bench.algorithmic_bytes("sort", [r], nw) == 300 * 32
-    assert bench.algorithmic_bytes("reduce", [r], nw) == 300 * 16 + 200 * 16
-    assert bench.algorithmic_bytes("merge", [r], nw) == 1000 * be + 200 * 16 + 1000 * be
+    sbar = bench.mean_cluster_size(2, False)
+    assert bench.algorithmic_bytes("scan", [r], nw, 2) == 1000 * 16
+    assert bench.algorithmic_bytes("sample", [r], nw, 2) == 2000 * sbar * be + 300 * 16
+    assert bench.algorithmic_bytes("sort", [r], nw, 2) == 300 * 32
+    assert bench.algorithmic_bytes("reduce", [r], nw, 2) == 300 * 16 + 200 * 16
+    assert bench.algorithmic_bytes("merge", [r], nw, 2) == 1000 * be + 200 * 16 + 1000 * be
+    # multi-spawn: owners are read once (visited entries, buffered clusters),
+    # not once per attempt
+    rf = dict(r, n_visit=800, n_clusters=50)
+    bc = 8 * nw + 24
+    assert bench.algorithmic_bytes("attempts", [rf], nw, 3, True, True) == 800 * be + 50 * bc + 300 * 16
+    assert bench.algorithmic_bytes("sample", [rf], nw, 3, True, True) == (
+        2000 * bench.mean_cluster_size(3, True) * be + 50 * bc)
     # averaged over records
     r2 = dict(r, n_sel=4000)
-    assert bench.algorithmic_bytes("sample", [r, r2], nw) == 3000 * 0.97 * be + 300 * 16
+    assert bench.algorithmic_bytes("sample", [r, r2], nw, 2) == 3000 * sbar * be + 300 * 16
 
 
-def test_read_traffic_from_profiles():
-    b, issue = bench.read_traffic("ueg14_m114_ccsdt_fnc_ms", "attempts")
-    assert b is not None and b > 0 and 0 < issue <= 100
-    assert bench.read_traffic("no_such_workload", "sample") == (None, None)
+def test_read_profile_and_rooflines(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic_toy.txt").write_text(
+        "# phase kernel unit dram_per_unit inst_per_unit issue_pct lanes\n"
+        "sample k_sample sample 10.0 2000.0 50.0 16.0\n"
+        "sort k_sort record 40.0 - - -\n"
+        "merge k_merge entry 64.0 - - -\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    p = bench.read_profile("toy")
+    assert p["sample"]["inst_per_unit"] == 2000.0 and p["sort"]["inst_per_unit"] is None
+    assert bench.read_profile("missing") == {}
+    r = dict(n_visit=0, nocc_after=1000, n_spawned=300, n_sel=2000, n_attempts=2000, n_keys=200, n_clusters=0)
+    pms = {"scan": 0.2, "sample": 4.0, "attempts": 0.0, "sort": 0.4, "reduce": 0.2, "merge": 0.4, "finalize": 0.0}
+    roof, ann = bench.roofline_objects("toy", pms, 2, [[r, r]], [2], [2], False, False)
+    hbm, mhz, _ = bench.peaks()
+    assert roof["bound"] == "alu" and roof["kernel"] == "sample"
+    # achieved = instructions per sample x samples / the phase time per step
+    assert abs(roof["achieved"] - 2000.0 * 2000 / 2.0e-3 / 1e9) < 1e-9
+    assert abs(roof["frac"] - roof["achieved"] / bench.lane_issue_peak(mhz)) < 1e-12
+    assert roof["traffic"] == 10.0 * 2000
+    assert ann["traffic"] is None            # the reduce kernel has no figure in the toy profile
+    alg = sum(bench.algorithmic_bytes(q, [r, r], 2, 2) for q in ("scan", "sort", "reduce", "merge"))
+    assert abs(ann["achieved"] - alg / 0.6e-3 / 1e9) < 1e-6
 
 
 def test_oracle_on_several_cores_small_workload():
@@ -51,5 +89,5 @@ def test_oracle_on_several_cores_small_workload():
     from ccmc_inputs import workload
 
     w = workload("ueg14_m38_ccsd")
-    v, kps, cores, secs, nslices = bench.oracle_all_cores(w, 0, 2, cores=2, per_slice=2000)
-    assert cores == 2 and v > 0 and secs > 0 and nslices >= 1 and kps >= 0
+    v, kps, cores, secs, rates, nslices, count = bench.oracle_all_cores(w, 0.3, cores=2, per_slice=2000)
+    assert cores == 2 and v > 0 and secs > 0 and nslices >= 1 and kps >= 0 and count >= 1 and len(rates) == 2

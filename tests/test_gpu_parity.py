@@ -40,7 +40,12 @@ def _oracle_system(w):
 
 
 def _pair(ccmc, w, **over):
+    """The oracle and a GPU context for one workload.  The GPU context sends
+    every spawned record through the sort (sort_all) unless the caller asks
+    for the default direct accumulation, so that its spawned multiset can be
+    compared with the oracle's."""
     w = dict(w)
+    w.setdefault("sort_all", True)
     w.update(over)
     so = _oracle_system(w)
     keys = ("tau", "target_pop", "d0_init", "shift_a", "zeta", "spawn_cutoff", "fnc", "multispawn", "a_thresh",
@@ -78,13 +83,15 @@ def _same_spawned(sim, ctx):
 
 
 def _run_lockstep(sim, ctx, nsteps, check_spawned_every=10):
+    """Steps both sides together; records and lists must agree after every
+    step, spawned multisets every check_spawned_every steps (0: never)."""
     for k in range(nsteps):
         # death deltas belong to the list at the step start: take the oracle's before stepping
         rec = sim.step()
         ctx.step(1)
         grec = ctx.records()[-1]
         _same_record(rec, grec)
-        if k % check_spawned_every == 0:
+        if check_spawned_every and k % check_spawned_every == 0:
             gk, gp = ctx.get_spawned()
             ok_, op_ = sim.spawned()
             a = np.lexsort((op_, ok_))
@@ -194,10 +201,12 @@ def test_molecule_full_size_step_bitexact(ccmc):
     """The synthetic molecule (20 electrons, 82 spin-orbitals, CCSDTQ, two-word
     determinants) at full size: about 4e6 occupied excitors of levels 0-4 and
     N_total of about 1.2e7, one step in the production launch configuration.
-    Spawned records, death deltas, the merged list and the record must match."""
+    The step size 0.005 (larger than the benchmark's) makes the annihilation
+    heavy: about 7.7e6 spawned records.  Spawned records, death deltas, the
+    merged list and the record must match."""
     from ccmc_inputs import molecule_state
 
-    w = workload("mol20_m82_ccsdtq")
+    w = workload("mol20_m82_ccsdtq", tau=0.005)
     h1, eri = molecule_integrals(norb=41, nocc=10, seed=7)
     w.update(h1=h1, eri=eri, nso=82)
     so, sim, ctx = _pair(ccmc, w)
@@ -215,17 +224,69 @@ def test_molecule_full_size_step_bitexact(ccmc):
     _same_list(sim, ctx)
 
 
-def test_molecule_all_samplers_bitexact(ccmc):
+@pytest.mark.parametrize("sort_all", [True, False])
+def test_molecule_all_samplers_bitexact(ccmc, sort_all):
     """A small molecule-like Hamiltonian (singles exist, so composite clusters
-    collapse onto the truncated space and composite death is exercised)."""
+    collapse onto the truncated space and composite death is exercised), with
+    every record sorted and with direct accumulation onto listed determinants."""
     h1, eri = molecule_integrals(norb=8, nocc=3, seed=5, scale=0.1)
     base = dict(kind="generic", nel=6, norb=8, nso=16, lmax=3, h1=h1, eri=eri, tau=0.01, target_pop=3000.0,
                 d0_init=400.0, shift_a=10, zeta=0.05, spawn_cutoff=2.0 ** -7, a_thresh=1.0, seed=3, replica=0)
     for fnc, ms in [(0, 0), (1, 0), (0, 1), (1, 1)]:
         w = dict(base, fnc=fnc, multispawn=ms)
-        so, sim, ctx = _pair(ccmc, w)
-        _run_lockstep(sim, ctx, 80, check_spawned_every=20)
+        so, sim, ctx = _pair(ccmc, w, sort_all=sort_all)
+        _run_lockstep(sim, ctx, 80, check_spawned_every=20 if sort_all else 0)
+        if not sort_all:
+            assert sum(r["n_direct"] for r in ctx.records()) > 0
         ctx.close()
+
+
+def test_direct_accumulation_lockstep_ueg114(ccmc):
+    """The annihilation fast path (records onto listed determinants added with
+    integer atomics, only new keys sorted) on the 114 spin-orbital FNC +
+    multi-spawn run: 300 steps in lockstep with the oracle, records and lists
+    bit for bit; most records take the fast path once the list has grown."""
+    w = workload("ueg14_m114_ccsdt_fnc_ms")
+    so, sim, ctx = _pair(ccmc, w, sort_all=False)
+    direct = total = 0
+    for k in range(300):
+        rec = sim.step()
+        ctx.step(1)
+        g = ctx.records()[-1]
+        _same_record(rec, g)
+        direct += g["n_direct"]
+        total += g["n_spawned"]
+        if k % 25 == 0:
+            _same_list(sim, ctx)
+    _same_list(sim, ctx)
+    assert 0 < direct < total and direct > total // 2
+
+
+def test_direct_accumulation_fp32_gas_at_scale(ccmc):
+    """The 162 spin-orbital FP32 gas (15,769 determinants, all of them
+    occupied at scale) grown on the GPU to a population of 10^6, then two
+    steps on both sides from the GPU's state: records and lists bit for bit,
+    nearly every record added directly."""
+    w = workload("ueg54_m162_ccsd_fp32", target_pop=1e6, d0_init=1e4)
+    so, sim, _ = _pair(ccmc, w)
+    ctx = ccmc.from_workload(w)
+    for _ in range(40):
+        ctx.step(10)
+        if ctx.get_state()[2]:
+            break
+    ctx.step(20)
+    bits, _, pop = ctx.get_list()
+    it, shift, vary, nprev = ctx.get_state()
+    sim.set_list_words(bits, pop)
+    sim.set_state(it, shift, bool(vary), nprev)
+    ctx.records()
+    for _ in range(2):
+        rec = sim.step()
+        ctx.step(1)
+        g = ctx.records()[-1]
+        _same_record(rec, g)
+        assert g["n_spawned"] > 100_000 and g["n_direct"] > 0.9 * g["n_spawned"]
+    _same_list(sim, ctx)
 
 
 def test_three_word_determinants_bitexact(ccmc):
@@ -233,6 +294,15 @@ def test_three_word_determinants_bitexact(ccmc):
     w = workload("ueg54_m162_ccsd_fp32", precision="fp64", target_pop=1e5, d0_init=200.0)
     so, sim, ctx = _pair(ccmc, w)
     _run_lockstep(sim, ctx, 25, check_spawned_every=5)
+
+
+def test_six_word_determinants_bitexact(ccmc):
+    """14 e / 358 spin-orbitals (six words per determinant), CCSDTQ, full
+    non-composite sampling with multi-spawn, grown from the reference."""
+    w = workload("ueg14_m358_ccsdtq", target_pop=3e4, d0_init=200.0)
+    so, sim, ctx = _pair(ccmc, w)
+    _run_lockstep(sim, ctx, 30, check_spawned_every=5)
+    assert len(ctx.get_list()[1]) > 1000
 
 
 def test_fp32_form_ueg38_bitexact(ccmc):

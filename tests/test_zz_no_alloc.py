@@ -60,7 +60,7 @@ def test_noalloc_reduce_matches_step_records():
     from ccmc_inputs import workload
 
     lib = ccmc.load()
-    ctx = ccmc.from_workload(workload("ueg14_m114_ccsdt_fnc_ms"))
+    ctx = ccmc.from_workload(workload("ueg14_m114_ccsdt_fnc_ms"), sort_all=True)
     rng = np.random.default_rng(5)
     stream = torch.cuda.current_stream()
     for call in range(2):
