@@ -197,6 +197,71 @@ def read_profile(workload: str) -> dict:
     return out
 
 
+PHASE_OF_KERNEL = [("k_scan", "scan"), ("k_sample", "sample"), ("k_attempts", "attempts"), ("k_sort", "sort"),
+                   ("k_seg", "reduce"), ("k_part_scan", "reduce"), ("k_merge", "merge"), ("k_keep", "merge"),
+                   ("k_scatter", "merge"), ("k_finalize", "finalize")]
+UNIT_OF_PHASE = {"scan": "entry", "sample": "sample", "attempts": "attempt", "sort": "record", "reduce": "record",
+                 "merge": "entry", "finalize": "step"}
+
+
+def summarize_ncu(csv_path: str, records_path: str, out_path: str, command: str):
+    """Writes profiles/traffic_<workload>.txt from an ncu --csv capture of one
+    step's kernels (metrics gpu__time_duration.sum, dram__bytes_read.sum,
+    dram__bytes_write.sum, smsp__inst_executed.sum, smsp__thread_inst_executed.sum,
+    smsp__issue_active.avg.pct_of_peak_sustained_active) and the records of
+    the captured step (bench.py --records-out): per phase the DRAM bytes and
+    thread instructions per unit (sample, attempt, record, list entry), the
+    time-weighted issue activity and the lanes per warp instruction."""
+    import csv
+
+    rows = {}
+    with open(csv_path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for r in csv.DictReader(lines):
+        key = (r["ID"], r["Kernel Name"])
+        try:
+            v = float(r["Metric Value"].replace(",", ""))
+        except ValueError:
+            continue
+        unit = r.get("Metric Unit", "")
+        scale = {"Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "byte": 1.0, "usecond": 1e-6, "msecond": 1e-3,
+                 "nsecond": 1e-9, "second": 1.0}.get(unit, 1.0)
+        rows.setdefault(key, {})[r["Metric Name"]] = v * scale
+    recs = json.load(open(records_path))
+    rec = recs[0] if isinstance(recs, list) else recs
+    per = {}
+    for (kid, name), m in rows.items():
+        short = name.split("(")[0].split("<")[0].replace("ccmc::", "").replace("void ", "").strip()
+        ph = next((p for pre, p in PHASE_OF_KERNEL if short.startswith(pre)), None)
+        if ph is None:
+            continue
+        a = per.setdefault(ph, {"dram": 0.0, "tinst": 0.0, "inst": 0.0, "t": 0.0, "issue_t": 0.0, "top": (0.0, short)})
+        t = m.get("gpu__time_duration.sum", 0.0)
+        a["dram"] += m.get("dram__bytes_read.sum", 0.0) + m.get("dram__bytes_write.sum", 0.0)
+        a["tinst"] += m.get("smsp__thread_inst_executed.sum", 0.0)
+        a["inst"] += m.get("smsp__inst_executed.sum", 0.0)
+        a["t"] += t
+        a["issue_t"] += t * m.get("smsp__issue_active.avg.pct_of_peak_sustained_active", 0.0)
+        if t > a["top"][0]:
+            a["top"] = (t, short)
+    with open(out_path, "w") as f:
+        f.write("# Per-unit ncu figures of one CCMC step's kernels, by phase (bench.py --summarize-ncu).\n")
+        f.write(f"# command: {command}\n")
+        f.write("# step units: " + json.dumps({k: rec[k] for k in ("n_sel", "n_visit", "n_attempts", "n_spawned",
+                                                                    "n_direct", "n_keys", "nocc_after")}) + "\n")
+        f.write("# phase kernel(longest) unit dram_bytes_per_unit thread_inst_per_unit issue_active_pct "
+                "lanes_per_inst\n")
+        for ph in ("scan", "sample", "attempts", "sort", "reduce", "merge", "finalize"):
+            if ph not in per:
+                continue
+            a = per[ph]
+            u = max(1.0, float(phase_units(ph, rec)))
+            issue = a["issue_t"] / a["t"] if a["t"] else 0.0
+            lanes = a["tinst"] / a["inst"] if a["inst"] else 0.0
+            f.write(f"{ph:9s} {a['top'][1]:18s} {UNIT_OF_PHASE[ph]:8s} {a['dram'] / u:14.3f} {a['tinst'] / u:14.3f} "
+                    f"{issue:6.1f} {lanes:6.2f}\n")
+
+
 def roofline_objects(name: str, pms: dict, nprof: int, precs_by_ctx: list, nw_by_ctx: list, lmax_by_ctx: list,
                      fnc: bool, multispawn: bool):
     """(roofline of the dominant kernel, HBM roofline of the annihilation and
@@ -537,6 +602,9 @@ def run_gpu(args, w, dist, rank, world, local):
         dist.barrier()
     clk = clocks.stop()
     recs = ctx.records()[-args.steps:]
+    if args.records_out and rank == 0:
+        with open(args.records_out, "w") as f:
+            json.dump(recs, f)
     _, _, launches1 = ctx.phase_times()
     ms_total = sum(times)
     samples = sum(r["n_sel"] + r["n_visit"] for r in recs)
@@ -741,6 +809,12 @@ def run_gpu_batched(args, local):
         clk = clocks.stop()
         _, _, launches1 = batch.phase_times()
         recs = [c.records()[-args.steps:] for c in ctxs]
+        if args.records_out:
+            # the batch's units: every replica's records summed per step
+            tot = [{k: sum(rr[i][k] for rr in recs) for k in recs[0][0] if k not in ("shift", "e_num")}
+                   for i in range(len(recs[0]))]
+            with open(args.records_out, "w") as f:
+                json.dump(tot, f)
         samples = sum(r["n_sel"] + r["n_visit"] for rr in recs for r in rr)
         keys = sum(r["n_spawned"] for rr in recs for r in rr)
         final = [c.get_list() for c in ctxs]
@@ -845,7 +919,14 @@ def main():
     ap.add_argument("--target-pop", type=float, default=0.0, help="override the workload's target population")
     ap.add_argument("--profile-window", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    ap.add_argument("--records-out", default="", help="write the timed steps' records (JSON) to this file")
+    ap.add_argument("--summarize-ncu", nargs=3, metavar=("CSV", "RECORDS", "OUT"),
+                    help="write a per-phase traffic summary from an ncu CSV and the captured step's records")
+    ap.add_argument("--ncu-command", default="", help="the capture command, quoted in the summary")
     args = ap.parse_args()
+    if args.summarize_ncu:
+        summarize_ncu(*args.summarize_ncu, command=args.ncu_command)
+        return
     from ccmc_inputs import batched_replicas, workload
 
     over = {}

@@ -45,6 +45,14 @@ WORKLOADS = {
     "mol20_m82_ccsdtq": dict(kind="generic", nel=20, norb=41, lmax=4, target_pop=1.0e7,
                              tau=2.0e-6, nsteps=50, seed=1, molecule_seed=7, d0_init=2.0e6,
                              equilibrate=400, list_capacity=40_000_000, state_seed=31),
+    # UEG 14 e / 66 spin-orbitals (33 plane waves), CCSDT with full
+    # non-composite sampling, r_s = 0.5 and 5: the systems of the paper's
+    # parallelisation-bias study (Sec. III.B, Fig. bias; CISDT space 22,969),
+    # run with the simulated distribution over processors (n_ranks, nu_move).
+    "ueg14_m66_ccsdt_rs0.5": dict(kind="ueg", nel=14, nso=66, rs=0.5, lmax=3, target_pop=2.0e5,
+                                  tau=0.001, nsteps=20000, seed=1, fnc=True, d0_init=1.0e3),
+    "ueg14_m66_ccsdt_rs5": dict(kind="ueg", nel=14, nso=66, rs=5.0, lmax=3, target_pop=2.0e5,
+                                tau=0.001, nsteps=20000, seed=1, fnc=True, d0_init=1.0e3),
     # UEG 14 e / 358 spin-orbitals (179 plane waves, |n|^2 <= 12; six-word
     # determinants), r_s = 1, CCSDTQ: the system of the paper's published
     # correlation energy (Sec. III.B), full non-composite + multi-spawn.

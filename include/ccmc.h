@@ -116,6 +116,11 @@ typedef struct {
     void *alloc_user;
     int32_t radix_bits;      /* digit width of the radix sort, 0 = default */
     int32_t flags;           /* CCMC_NO_GRAPH, CCMC_SORT_ALL (below) */
+    int32_t n_ranks;         /* simulated processors N_p of the paper's distributed
+                                cluster sampling (Sec. III, Eq. ccmc_dist); 0 or 1:
+                                none (the plain single-GPU step) */
+    int32_t nu_move;         /* excitors move between the simulated processors every
+                                2^nu_move iterations; >= 64: never */
 } ccmc_params;
 
 /* ccmc_params.flags
@@ -325,6 +330,32 @@ void ccmc_batch_free(ccmc_batch *b);
  * serialised by the caller. */
 ccmc_status ccmc_reduce_records_noalloc(const uint64_t *keys_in, const int64_t *pops_in, size_t n, int32_t key_bits,
                                         uint64_t *keys_out, int64_t *pops_out, size_t *n_out, void *cuda_stream);
+
+/* ---- The paper's distribution over processors, simulated ----------------
+ * Sec. III distributes excitors over N_p processors with the owner
+ *   o(D, i) = (hash(D) + i) >> nu_move,  p(D, i) = hash(D xor o) mod N_p
+ * (Eq. ccmc_dist; i the iteration, o xor-ed into the first word of D), and
+ * each processor forms composite clusters only from its own excitors.  Here
+ * the hash is Philox-4x64-10 under a fixed key used as a mixing function over
+ * the bit string (three words per call, each call chained through the fourth
+ * counter word).  With ccmc_params.n_ranks = N_p > 1 the step keeps a
+ * composite cluster of size s only if all its excitors have the same owner at
+ * the current iteration, and multiplies its amplitude by N_p^(s-1) (the
+ * inverse of the co-location probability), so that the step is unbiased
+ * averaged over owners while each iteration samples a subspace -- the source
+ * of the parallelisation bias the paper studies.
+ *
+ * ccmc_colocation computes the co-location statistics of Fig. excitdistrib
+ * for n determinants (host array, n rows of n_words words): for every
+ * checkpoint T (ascending, at most 64, the last <= 2^20), the sums over pairs
+ * i < j of C_ij(T) and C_ij(T)^2, C_ij(T) being the number of iterations
+ * t < T at which excitors i and j have the same owner.  The mean co-location
+ * probability is sum_c / (P T) and its variance over pairs
+ * sum_c2 / (P T^2) - mean^2, with P = n(n-1)/2.  n_ranks <= 65535, n <= 2^20.
+ * Allocates temporary device memory; synchronises cuda_stream. */
+ccmc_status ccmc_colocation(const uint64_t *dets, size_t n, int32_t n_words, int64_t n_ranks, int32_t nu_move,
+                            const int64_t *checkpoints, int32_t n_checkpoints, uint64_t *sum_c, uint64_t *sum_c2,
+                            void *cuda_stream);
 
 /* Waits for the context's stream and reports kernel-detected errors. */
 ccmc_status ccmc_sync(ccmc_ctx *ctx);

@@ -51,10 +51,12 @@ class Params(ctypes.Structure):
         ("zeta", c_double),
         ("spawn_cutoff", c_double),
         ("multispawn", c_int32),
-        ("pad0", c_int32),
+        ("n_ranks", c_int32),
         ("a_thresh", c_double),
         ("seed", c_uint64),
         ("replica", c_uint64),
+        ("nu_move", c_int32),
+        ("pad1", c_int32),
     ]
 
 
@@ -110,6 +112,9 @@ def lib():
             "orc_key_bound": (c_uint64, [c_void_p]),
             "orc_excite": (c_int, [c_void_p, u64p, u64p, u64p, dp, dp]),
             "orc_philox": (None, [u64p, u64p, u64p]),
+            "orc_det_hash": (c_uint64, [u64p, c_int]),
+            "orc_owner": (c_uint64, [u64p, c_int, c_uint64, c_int, c_uint64]),
+            "orc_colocation": (None, [u64p, c_int64, c_int, c_int64, c_int, c_int64, i64p, c_int, u64p, u64p]),
             "orc_size_draw": (c_int, [c_uint64, c_int, c_int]),
             "orc_pick_index": (c_int64, [i64p, c_int64, c_uint64]),
             "orc_below": (c_uint64, [c_uint64, c_uint64]),
@@ -147,6 +152,31 @@ def _u64(a):
 def _i64(a):
     a = np.ascontiguousarray(a, dtype=np.int64)
     return a, a.ctypes.data_as(POINTER(c_int64))
+
+
+def det_hash(words) -> int:
+    """The determinant hash of the simulated distribution (Sec. III)."""
+    w, wp = _u64(words)
+    return int(lib().orc_det_hash(wp, len(w)))
+
+
+def owner(words, it: int, nu_move: int, n_ranks: int) -> int:
+    """Processor of an excitor at iteration it (Sec. III, Eq. ccmc_dist)."""
+    w, wp = _u64(words)
+    return int(lib().orc_owner(wp, len(w), c_uint64(it), nu_move, c_uint64(n_ranks)))
+
+
+def colocation(dets: np.ndarray, n_ranks: int, nu_move: int, checkpoints) -> tuple:
+    """Sums over excitor pairs of C_ij(T) and C_ij(T)^2 at each checkpoint T,
+    C_ij(T) = iterations t < T with i and j on the same processor."""
+    d = np.ascontiguousarray(dets, dtype=np.uint64)
+    ck = np.ascontiguousarray(checkpoints, dtype=np.int64)
+    s1 = np.zeros(len(ck), dtype=np.uint64)
+    s2 = np.zeros(len(ck), dtype=np.uint64)
+    lib().orc_colocation(d.ctypes.data_as(POINTER(c_uint64)), d.shape[0], d.shape[1], n_ranks, nu_move,
+                         int(ck[-1]), ck.ctypes.data_as(POINTER(c_int64)), len(ck),
+                         s1.ctypes.data_as(POINTER(c_uint64)), s2.ctypes.data_as(POINTER(c_uint64)))
+    return s1, s2
 
 
 def philox(ctr, key) -> np.ndarray:
@@ -325,7 +355,9 @@ def default_params(**kw) -> Params:
     p.zeta = kw.get("zeta", 0.05)
     p.spawn_cutoff = kw.get("spawn_cutoff", 2.0 ** -7)
     p.multispawn = int(kw.get("multispawn", 0))
-    p.pad0 = 0
+    p.n_ranks = int(kw.get("n_ranks", 1))
+    p.nu_move = int(kw.get("nu_move", 64))
+    p.pad1 = 0
     p.a_thresh = kw.get("a_thresh", 1.0)
     p.seed = kw.get("seed", 1)
     p.replica = kw.get("replica", 0)

@@ -86,6 +86,74 @@ void orc_philox(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
+/* ------------------------------------------------------------------------- */
+/* The paper's distribution of excitors over N_p processors (Sec. III,       */
+/* Eq. ccmc_dist), simulated: a determinant hash (any good hash will do;     */
+/* here Philox-4x64-10 under a fixed key used as a mixing function over the  */
+/* bit string, three words per call, each call taking the previous result as */
+/* its fourth counter word) and the owner                                    */
+/*   o(D, i) = (hash(D) + i) >> nu_move,   p(D, i) = hash(D xor o) mod N_p,  */
+/* with o xor-ed into the first word of the bit string.                     */
+/* ------------------------------------------------------------------------- */
+
+static const uint64_t HASH_KEY[2] = { 0x243F6A8885A308D3ULL, 0x13198A2E03707344ULL };
+
+static uint64_t det_hash(const uint64_t *w, int nw)
+{
+    uint64_t h = 0;
+    for (int g = 0; g < nw; g += 3) {
+        uint64_t c[4] = { w[g], g + 1 < nw ? w[g + 1] : 0, g + 2 < nw ? w[g + 2] : 0, h }, out[4];
+        orc_philox(c, HASH_KEY, out);
+        h = out[0];
+    }
+    return h;
+}
+
+uint64_t orc_det_hash(const uint64_t *w, int nw) { return det_hash(w, nw); }
+
+uint64_t orc_owner(const uint64_t *w, int nw, uint64_t iter, int nu_move, uint64_t n_ranks)
+{
+    uint64_t h = det_hash(w, nw);
+    uint64_t o = nu_move >= 64 ? 0 : (h + iter) >> nu_move;
+    uint64_t x[OW];
+    for (int i = 0; i < nw; i++) x[i] = w[i];
+    x[0] ^= o;
+    return det_hash(x, nw) % n_ranks;
+}
+
+/* Co-location of excitor pairs (Fig. excitdistrib): for T = 1..t_max, the
+   sums over pairs i < j of C_ij(T) and C_ij(T)^2, where C_ij(T) counts the
+   iterations t < T at which excitors i and j have the same owner; reported
+   at the nck checkpoints tcheck[] (ascending). */
+void orc_colocation(const uint64_t *dets, int64_t n, int nw, int64_t n_ranks, int nu_move, int64_t t_max,
+                    const int64_t *tcheck, int nck, uint64_t *sum_c, uint64_t *sum_c2)
+{
+    int64_t *own = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n * t_max));
+    int64_t *cnt = (int64_t *)calloc((size_t)(n * (n - 1) / 2 + 1), sizeof(int64_t));
+    for (int64_t t = 0; t < t_max; t++)
+        for (int64_t i = 0; i < n; i++)
+            own[t * n + i] = (int64_t)orc_owner(dets + i * nw, nw, (uint64_t)t, nu_move, (uint64_t)n_ranks);
+    for (int k = 0; k < nck; k++) { sum_c[k] = 0; sum_c2[k] = 0; }
+    int k = 0;
+    for (int64_t t = 0; t < t_max && k < nck; t++) {
+        int64_t q = 0;
+        for (int64_t i = 0; i < n; i++)
+            for (int64_t j = i + 1; j < n; j++, q++)
+                if (own[t * n + i] == own[t * n + j]) cnt[q]++;
+        while (k < nck && tcheck[k] == t + 1) {
+            q = 0;
+            for (int64_t i = 0; i < n; i++)
+                for (int64_t j = i + 1; j < n; j++, q++) {
+                    sum_c[k] += (uint64_t)cnt[q];
+                    sum_c2[k] += (uint64_t)(cnt[q] * cnt[q]);
+                }
+            k++;
+        }
+    }
+    free(own);
+    free(cnt);
+}
+
 static void draw4(const uint64_t key[2], uint64_t it, uint64_t tag, uint64_t index,
                   uint64_t block, uint64_t out[4])
 {
@@ -878,10 +946,12 @@ typedef struct {
     double zeta;
     double spawn_cutoff;
     int32_t multispawn;
-    int32_t pad0;
+    int32_t n_ranks;      /* processors of the simulated distribution (<= 1: none) */
     double a_thresh;
     uint64_t seed;
     uint64_t replica;
+    int32_t nu_move;      /* owners move every 2^nu_move iterations (>= 64: never) */
+    int32_t pad1;
 } orc_params;
 
 typedef struct {
@@ -1111,6 +1181,13 @@ static int sample_cluster(orc_sim *m, uint64_t g, const int64_t *prefix, int64_t
             ex[e] = m->bits[idx[e]];
             if (m->pop[idx[e]] < 0) neg ^= 1;
         }
+        /* simulated distribution (Sec. III): a composite cluster is formed
+           only from excitors on one processor at this iteration */
+        if (sz >= 2 && m->prm.n_ranks > 1) {
+            uint64_t own0 = orc_owner(ex[0].w, s->nw, m->iter, m->prm.nu_move, (uint64_t)m->prm.n_ranks);
+            for (int e = 1; e < sz; e++)
+                if (orc_owner(ex[e].w, s->nw, m->iter, m->prm.nu_move, (uint64_t)m->prm.n_ranks) != own0) return 0;
+        }
         if (!collapse(s, sz, ex, &dj, &sigma)) return 0;
         if (n0 < 0 && ((sz - 1) & 1)) neg ^= 1;
         amp = neg ? -mag[sz] : mag[sz];
@@ -1299,6 +1376,13 @@ static int sim_step_range(orc_sim *m, int propagate_only, int64_t i_lo, int64_t 
         den = den * p;
         den = den * fact;
         mag[sz] = num / den;
+        /* with N_p simulated processors a composite cluster is co-located
+           with probability N_p^-(s-1): its amplitude carries N_p^(s-1) */
+        if (sz >= 2 && m->prm.n_ranks > 1) {
+            double f = 1.0;
+            for (int e = 1; e < sz; e++) f = f * (double)m->prm.n_ranks;
+            mag[sz] = mag[sz] * f;
+        }
     }
     int rc = 0;
     if (m->prm.fnc) {

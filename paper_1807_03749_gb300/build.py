@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libccmc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-UNITS = ["ccmc_step.cu", "ccmc_api.cu"] + [f"ccmc_step_k{k}.cu" for k in range(1, 7)]
+UNITS = ["ccmc_step.cu", "ccmc_api.cu", "ccmc_dist.cu"] + [f"ccmc_step_k{k}.cu" for k in range(1, 7)]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -43,7 +43,7 @@ class Params(ctypes.Structure):
                 ("precision", c_int32), ("a_thresh", c_double), ("seed", c_uint64), ("replica", c_uint64),
                 ("list_capacity", c_uint64), ("spawn_capacity", c_uint64), ("cuda_stream", c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", c_void_p), ("radix_bits", c_int32),
-                ("flags", c_int32)]
+                ("flags", c_int32), ("n_ranks", c_int32), ("nu_move", c_int32)]
 
 
 class Record(ctypes.Structure):
@@ -69,7 +69,7 @@ EXPORTS = [
     "ccmc_get_list", "ccmc_set_list", "ccmc_get_spawned", "ccmc_get_death", "ccmc_set_state", "ccmc_get_state",
     "ccmc_save", "ccmc_load", "ccmc_sync", "ccmc_last_error", "ccmc_free", "ccmc_profile", "ccmc_phase_times",
     "ccmc_reduce_records_noalloc", "ccmc_batch_create", "ccmc_step_batched", "ccmc_batch_info", "ccmc_batch_free",
-    "ccmc_batch_profile", "ccmc_batch_phase_times",
+    "ccmc_batch_profile", "ccmc_batch_phase_times", "ccmc_colocation",
 ]
 
 PHASES = ["scan", "sample", "attempts", "sort", "reduce", "merge", "finalize"]
@@ -111,6 +111,7 @@ def load(path: str | None = None):
         "ccmc_batch_free": (None, [vp]),
         "ccmc_batch_profile": (c_int, [vp, c_int32]),
         "ccmc_batch_phase_times": (c_int, [vp, dp, i64p, c_int32, i64p]),
+        "ccmc_colocation": (c_int, [u64p, c_size_t, c_int32, c_int64, c_int32, i64p, c_int32, u64p, u64p, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -150,7 +151,7 @@ class Context:
                  multispawn: bool = False, a_thresh: float = 1.0, seed: int = 1, replica: int = 0,
                  precision: str = "fp64", list_capacity: int = 0, spawn_capacity: int = 0, stream=None,
                  use_torch_allocator: bool = False, radix_bits: int = 0, use_graph: bool = True,
-                 sort_all: bool = False, **_ignored):
+                 sort_all: bool = False, n_ranks: int = 1, nu_move: int = 64, **_ignored):
         L = load()
         self._lib = L
         self.nel, self.nso, self.lmax = nel, nso, lmax
@@ -177,6 +178,7 @@ class Context:
         p.list_capacity, p.spawn_capacity = list_capacity, spawn_capacity
         p.radix_bits = radix_bits
         p.flags = (0 if use_graph else 1) | (2 if sort_all else 0)
+        p.n_ranks, p.nu_move = n_ranks, nu_move
         if stream is not None:
             p.cuda_stream = c_void_p(int(stream))
         if use_torch_allocator:
@@ -370,6 +372,23 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def colocation(dets: np.ndarray, n_ranks: int, nu_move: int, checkpoints, stream=None):
+    """Co-location sums of the simulated distribution (ccmc_colocation): for
+    each checkpoint T, (sum over pairs of C_ij(T), sum of C_ij(T)^2)."""
+    L = load()
+    d = np.ascontiguousarray(dets, dtype=np.uint64)
+    if d.ndim == 1:
+        d = d.reshape(-1, 1)
+    ck = np.ascontiguousarray(checkpoints, dtype=np.int64)
+    s1 = np.zeros(len(ck), dtype=np.uint64)
+    s2 = np.zeros(len(ck), dtype=np.uint64)
+    st = L.ccmc_colocation(_ptr(d, c_uint64), d.shape[0], d.shape[1], n_ranks, nu_move, _ptr(ck, c_int64), len(ck),
+                           _ptr(s1, c_uint64), _ptr(s2, c_uint64), c_void_p(int(stream)) if stream else None)
+    if st != 0:
+        raise CCMCError(st, "ccmc_colocation failed")
+    return s1, s2
 
 
 def from_workload(w: dict, **overrides) -> Context:

@@ -395,6 +395,7 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     if (params->radix_bits < 0 || params->radix_bits > MAX_DIGIT_BITS) return CCMC_ERR_ARG;
     if (params->precision != CCMC_FP64 && params->precision != CCMC_FP32) return CCMC_ERR_ARG;
     if (params->precision == CCMC_FP32 && nso > 192) return CCMC_ERR_ARG;   // FP32 form: up to three words
+    if (params->n_ranks < 0 || params->nu_move < 0) return CCMC_ERR_ARG;
 
     ccmc_ctx *ctx = new (std::nothrow) ccmc_ctx();
     if (!ctx) return CCMC_ERR_OOM;
@@ -562,6 +563,8 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     rp.multispawn = params->multispawn ? 1 : 0;
     rp.a_thresh_one = params->a_thresh == 1.0 ? 1 : 0;
     rp.direct = (params->flags & CCMC_SORT_ALL) ? 0 : 1;
+    rp.nranks = params->n_ranks > 1 ? params->n_ranks : 1;
+    rp.nu_move = params->nu_move;
     {
         // work per step beyond which a runaway population is reported
         // instead of sampled: 64x the target, at least 2^24, at most 2^36
@@ -625,9 +628,11 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     cl.end = al.arr<i64>(cl.cap);
     WorkArrays &wa = ctx->sc.wa;
     const i64 lc = ctx->list_cap;
-    wa.prefix = al.arr<i64>(lc);
-    wa.tdeath = al.arr<double>(lc);
-    wa.href = al.arr<double>(lc);
+    {
+        // PickEntry<K> is 64 bytes for up to four words, 96 above
+        const size_t pe = K <= 4 ? 64 : 96;
+        wa.picks = al.get((size_t)lc * pe);
+    }
     wa.bucket_bits = 10;
     while (wa.bucket_bits < 22 && (1LL << wa.bucket_bits) < lc / 2) wa.bucket_bits++;
     wa.bucket = al.arr<int>(((size_t)1 << wa.bucket_bits) + 1);
@@ -641,6 +646,7 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     wa.hit = al.arr<unsigned char>(lc);
     wa.newpop = al.arr<i64>(lc);
     wa.keep_l = al.arr<i64>(lc);
+    wa.before = al.arr<int>(lc);
     wa.keep_s = al.arr<i64>(sp.cap);
     wa.ins = al.arr<i64>(sp.cap);
     wa.part = al.arr<i64>(4 * 2 * (size_t)std::max(sh.scan_grid, sh.work_grid));

@@ -157,6 +157,35 @@ __host__ __device__ __forceinline__ R4 draw(u64 k0, u64 k1, u64 it, u64 tag, u64
     return philox(it, (tag << 56) | index, block, 0, k0, k1);
 }
 
+// ---------------------------------------------------------------------------
+// The paper's distribution of excitors over N_p processors (Sec. III, Eq.
+// ccmc_dist), simulated on one GPU: a determinant hash (Philox-4x64-10 under
+// a fixed key as a mixing function over the bit string, three words per
+// call, each call taking the previous result as its fourth counter word)
+// and the owner o = (hash(D) + i) >> nu_move, p = hash(D xor o) mod N_p,
+// with o xor-ed into the first word; nu_move >= 64 never moves an excitor.
+// ---------------------------------------------------------------------------
+
+constexpr u64 HASH_K0 = 0x243F6A8885A308D3ULL, HASH_K1 = 0x13198A2E03707344ULL;
+
+__host__ __device__ __forceinline__ u64 words_hash(const u64 *w, int nw)
+{
+    u64 h = 0;
+    for (int g = 0; g < nw; g += 3)
+        h = philox(w[g], g + 1 < nw ? w[g + 1] : 0, g + 2 < nw ? w[g + 2] : 0, h, HASH_K0, HASH_K1).v[0];
+    return h;
+}
+
+__host__ __device__ __forceinline__ u64 words_owner(const u64 *w, int nw, u64 it, int nu_move, u64 n_ranks)
+{
+    const u64 h = words_hash(w, nw);
+    const u64 o = nu_move >= 64 ? 0 : (h + it) >> nu_move;
+    u64 x[6];
+    for (int i = 0; i < nw; i++) x[i] = w[i];
+    x[0] ^= o;
+    return words_hash(x, nw) % n_ranks;
+}
+
 // uniform in [0,1) from the top 53 bits
 __device__ __forceinline__ double unif(u64 r) { return (double)(r >> 11) * 0x1p-53; }
 

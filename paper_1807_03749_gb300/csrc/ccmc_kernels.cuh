@@ -247,7 +247,8 @@ __device__ __forceinline__ bool round_value(double x, u64 r, const RunParams &p,
 // smallest i in [1, n-1] with prefix[i] > x (excitor owning position x);
 // the bucket of x brackets the answer between the owners of its first
 // position and of the next bucket's first position
-__device__ __forceinline__ i64 pick_index(const i64 *prefix, const int *bucket, int shift, i64 nbuckets, i64 n,
+template <int K>
+__device__ __forceinline__ i64 pick_index(const PickEntry<K> *pk, const int *bucket, int shift, i64 nbuckets, i64 n,
                                           u64 x)
 {
     i64 b = (i64)(x >> shift);
@@ -255,7 +256,7 @@ __device__ __forceinline__ i64 pick_index(const i64 *prefix, const int *bucket, 
     i64 hi = b + 1 < nbuckets ? __ldg(&bucket[b + 1]) : n - 1;
     while (lo < hi) {
         i64 mid = lo + (hi - lo) / 2;
-        if ((u64)__ldg(&prefix[mid]) > x) hi = mid;
+        if ((u64)__ldg(&pk[mid].prefix) > x) hi = mid;
         else lo = mid + 1;
     }
     return lo;
@@ -336,22 +337,24 @@ __device__ __forceinline__ i64 lower_bound_key(const u64 *keys, i64 n, u64 k)
 // stochastic rounding and the rank key.  The expanded-attempt kernel queues
 // the surviving draws and finishes them 32 at a time, so the second half
 // runs on full warps.
+// the drawn excitation (holes i, j and particles a, b: 16 bits each, M <= 384)
 template <int K>
-__device__ __forceinline__ bool attempt_draw(const SysDev &s, const Det<K> &dj, const R4 &r, unsigned &code, int &gc)
+__device__ __forceinline__ bool attempt_draw(const SysDev &s, const Det<K> &dj, const R4 &r, u64 &code, int &gc)
 {
     Det<K> di;
     int nh, i, j, a, b;
     if (!excite(s, dj, r, di, nh, i, j, a, b, gc)) return false;
     if (level_of(s, di) > s.lmax) return false;
-    code = (unsigned)i | ((unsigned)j << 8) | ((unsigned)a << 16) | ((unsigned)b << 24);
+    code = (u64)i | ((u64)j << 16) | ((u64)a << 32) | ((u64)b << 48);
     return true;
 }
 
 template <int K, typename R>
 __device__ __forceinline__ bool attempt_finish(const SysDev &s, const RunParams &p, const Det<K> &dj, double c_att,
-                                               u64 r3, unsigned code, int gc, u64 &key, i64 &val, unsigned &err)
+                                               u64 r3, u64 code, int gc, u64 &key, i64 &val, unsigned &err)
 {
-    const int i = code & 255, j = (code >> 8) & 255, a = (code >> 16) & 255, b = code >> 24;
+    const int i = (int)(code & 0xFFFF), j = (int)((code >> 16) & 0xFFFF), a = (int)((code >> 32) & 0xFFFF),
+              b = (int)(code >> 48);
     const int nh = (gc == 1 || gc == 2) ? 1 : 2;
     Det<K> di = dj;
     flip(di, i);
@@ -379,13 +382,13 @@ struct AttQueue {
     u64 det[K][64];
     double c[64];
     u64 r[64];
-    unsigned code[64];
+    u64 code[64];
     unsigned char gc[64];
 };
 
 // All 32 lanes call; lanes with ok append their attempt (qn < 32 on entry).
 template <int K>
-__device__ __forceinline__ void q_push(AttQueue<K> &q, int &qn, bool ok, const Det<K> &dj, double c, u64 r3, unsigned code,
+__device__ __forceinline__ void q_push(AttQueue<K> &q, int &qn, bool ok, const Det<K> &dj, double c, u64 r3, u64 code,
                                        int gc)
 {
     const int lane = threadIdx.x & 31;
@@ -618,7 +621,11 @@ __device__ __forceinline__ void d_scan_top(const ListView &L, DevStep *st, const
         // the list's key range, within the table's capacity
         st->n_direct = 0;
         st->n_hit = 0;
-        if (p.direct && st->n_occ > 0) {
+        // direct accumulation pays once the step spawns more than about one
+        // record per ten list entries (the buckets cost a pass over the
+        // list, a sorted record several); the choice follows the previous
+        // step and does not change any result
+        if (p.direct && st->n_occ > 0 && 10 * st->prev_spawned > st->n_occ) {
             const u64 kmax = L.key[st->n_occ - 1];
             i64 want = 2 * st->n_occ;
             if (want > (1LL << wa.kbucket_bits)) want = 1LL << wa.kbucket_bits;
@@ -655,6 +662,13 @@ __device__ __forceinline__ void d_scan_top(const ListView &L, DevStep *st, const
             den = den * pr;
             den = den * fact;
             st->mag[s] = num / den;
+            // N_p simulated processors: a composite cluster is co-located
+            // with probability N_p^-(s-1), so its amplitude carries N_p^(s-1)
+            if (s >= 2 && p.nranks > 1) {
+                double f = 1.0;
+                for (int e = 1; e < s; e++) f = f * (double)p.nranks;
+                st->mag[s] = st->mag[s] * f;
+            }
         }
         // every cluster of size s has |A| = mag[s]: its attempt count and
         // the magnitude of one attempt's coefficient, once per step
@@ -699,7 +713,10 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
         i64 iw = block_incl_scan(w, sm, tw);
         i64 ia = block_incl_scan(na, sm, ta);
         if (ok) {
-            wa.prefix[i] = cw + iw;
+            PickEntry<K> pe;
+            pe.prefix = cw + iw;
+            pe.pop = v;
+            pe.href = 0.0;
             if (i > 0 && w > 0) {
                 // buckets whose first position falls in [prefix[i-1], prefix[i]) start at entry i
                 const int k = st->bucket_shift;
@@ -708,6 +725,7 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
                 for (u64 b = b0; b < b1; b++) wa.bucket[b] = (int)i;
             }
             wa.acc[i] = 0;
+            wa.before[i] = 0;
             if (st->nkb > 0) {
                 // buckets whose first key falls in (key[i-1], key[i]] start at entry i
                 const int ks = st->kshift;
@@ -716,11 +734,13 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
                 wa.hit[i] = 0;
             }
             const double td = p.tau * ((i == 0 ? 0.0 : L.diag[i]) - S);
-            wa.tdeath[i] = td;
+            pe.tdeath = td;
+            const Det<K> d = load_det<K>(L.bits, L.cap, i);
+#pragma unroll
+            for (int q = 0; q < K; q++) pe.w[q] = d.w[q];
             i64 dv = 0;
             if (p.fnc) {
                 wa.att_end[i] = ca + ia;
-                Det<K> d = load_det<K>(L.bits, L.cap, i);
                 int sd = excitor_sign(s, d);
                 double coef = sd > 0 ? amp : -amp;
                 int lev = level_of(s, d);
@@ -732,10 +752,10 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
                 wa.catt[i] = na > 1 ? coef / (double)na : coef;
             } else {
                 // <HF|H|D_i> for the single-excitor clusters of the sampler
-                const Det<K> d = load_det<K>(L.bits, L.cap, i);
                 const int lev = level_of(s, d);
-                wa.href[i] = (lev == 1 || lev == 2) ? h_ref<K, R>(s, d) : 0.0;
+                pe.href = (lev == 1 || lev == 2) ? h_ref<K, R>(s, d) : 0.0;
             }
+            ((PickEntry<K> *)wa.picks)[i] = pe;
             wa.death[i] = dv;
         }
         cw += tw;
@@ -788,6 +808,7 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
     i64 death_hf = 0;      // reference-cluster deaths, summed per block at the end
     i64 ndirect = 0;       // records added directly to listed determinants
     const DirectView dv = direct_view(L, wa, st);
+    const PickEntry<K> *pk = (const PickEntry<K> *)wa.picks;
     // each warp runs its 32 samples of every block tile on its own: the
     // appends are staged per warp, so no block barrier is needed in the loop
     for (i64 g0 = (i64)vb * blockDim.x + 32 * wid; g0 < n_sel; g0 += (i64)vg * blockDim.x) {
@@ -824,7 +845,7 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
                 // the picks are independent: issue all searches before using them
                 for (int e = 0; e < sz; e++) {
                     u64 rr = e < 2 ? r0.v[2 + e] : r1.v[e - 2];
-                    idx[e] = pick_index(wa.prefix, wa.bucket, bshift, nbk, n, below(rr, (u64)nex));
+                    idx[e] = pick_index<K>(pk, wa.bucket, bshift, nbk, n, below(rr, (u64)nex));
                 }
                 for (int e = 1; e < sz; e++)
                     for (int f = 0; f < e; f++)
@@ -833,15 +854,26 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
                     // one excitor: its own determinant, with the sign s_D of
                     // applying it to HF (the closed form of the same product)
                     const i64 id = idx[0];
-                    if (L.pop[id] < 0) neg ^= 1;
-                    dj = load_det<K>(L.bits, L.cap, id);
+                    if (__ldg(&pk[id].pop) < 0) neg ^= 1;
+#pragma unroll
+                    for (int q = 0; q < K; q++) dj.w[q] = __ldg(&pk[id].w[q]);
                     par = excitor_sign(s, dj) < 0 ? 1 : 0;
                 } else {
+                    u64 own0 = 0;
                     for (int e = 0; e < sz && valid; e++) {
                         const i64 id = idx[e];
-                        if (L.pop[id] < 0) neg ^= 1;
-                        Det<K> de = load_det<K>(L.bits, L.cap, id);
-                        if (!apply_excitor(s, de, dj, par)) valid = false;   // shared orbital
+                        if (__ldg(&pk[id].pop) < 0) neg ^= 1;
+                        Det<K> de;
+#pragma unroll
+                        for (int q = 0; q < K; q++) de.w[q] = __ldg(&pk[id].w[q]);
+                        if (p.nranks > 1) {
+                            // simulated distribution: a composite cluster is
+                            // formed only from excitors on one processor
+                            const u64 ow = words_owner(de.w, K, it, p.nu_move, (u64)p.nranks);
+                            if (e == 0) own0 = ow;
+                            else if (ow != own0) valid = false;
+                        }
+                        if (valid && !apply_excitor(s, de, dj, par)) valid = false;   // shared orbital
                     }
                 }
                 if (valid) {
@@ -855,11 +887,11 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
                 coef = (par & 1) ? -amp : amp;
                 // a single excitor collapses to its own determinant: <HF|H|D> cached per entry
                 if (lev == 1 || lev == 2)
-                    es.add(to_fix((sz == 1 && !p.fnc ? wa.href[idx0] : h_ref<K, R>(s, dj)) * coef));
+                    es.add(to_fix((sz == 1 && !p.fnc ? __ldg(&pk[idx0].href) : h_ref<K, R>(s, dj)) * coef));
                 // s_D of the collapsed determinant (HF: +1; one excitor: known)
                 const int sdj = sz == 0 ? 1 : (sz == 1 ? ((par & 1) ? -1 : 1) : excitor_sign(s, dj));
                 if (sz <= 1) {
-                    double x = wa.tdeath[idx0] * coef;   // tau (Delta E - S) C (idx0 = 0 for the reference)
+                    double x = __ldg(&pk[idx0].tdeath) * coef;   // tau (Delta E - S) C (idx0 = 0 for the reference)
                     if (sdj > 0) x = -x;
                     i64 dv;
                     if (!round_value(x, r0.v[1], p, false, dv)) err |= ERRB_NUMERIC;
@@ -913,7 +945,7 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
             // valid lanes together; the few that survive the generator and
             // the truncation wait in the queue and are finished 32 at a time
             bool ok = false;
-            unsigned code = 0;
+            u64 code = 0;
             int gc = 0;
             u64 r3 = 0;
             if (valid_cl) {
@@ -997,7 +1029,7 @@ __device__ __forceinline__ void d_attempts(const SysDev &s, const ListView &L, D
             Det<K> dj;
             double ca = 0.0;
             u64 r3 = 0;
-            unsigned code = 0;
+            u64 code = 0;
             int gc = 0;
             if (t0 + lane < a1) {
                 u64 tag, idx;
@@ -1252,6 +1284,8 @@ __device__ __forceinline__ void d_merge_match(const ListView &L, DevStep *st, co
             rpop[j] = v;
             wa.ins[j] = pos;
             wa.keep_s[j] = v != 0 ? 1 : 0;
+            // a kept new key lands right before list entry pos
+            if (v != 0 && pos < n) atomicAdd(&wa.before[pos], 1);
         }
     }
 }
@@ -1267,7 +1301,9 @@ __device__ __forceinline__ void d_merge_list(const ListView &L, DevStep *st, con
         i64 v = L.pop[i] + wa.death[i] + wa.acc[i];
         if (i > 0) v = threshold(p, it, L.key[i], v);
         wa.newpop[i] = v;
-        wa.keep_l[i] = (i == 0 || v != 0) ? 1 : 0;
+        // two counts in one word (each below 2^31): the entry's keep flag and
+        // the kept new keys that go before it; one prefix gives both
+        wa.keep_l[i] = ((i == 0 || v != 0) ? 1 : 0) | ((i64)wa.before[i] << 32);
         if (direct) hits += wa.hit[i];
     }
     if (direct) {
@@ -1324,7 +1360,7 @@ __device__ __forceinline__ void d_keep_top(DevStep *st, const WorkArrays &wa, in
     i64 ib = block_incl_scan(b, sm, tb);
     if (t < G) wa.part[4 * (G + t) + 2] = ib - b;
     if (t == 0) {
-        st->kept_list = ta;
+        st->kept_list = ta & 0xFFFFFFFFLL;   // the low count of the packed list flags
         st->kept_new = tb;
     }
 }
@@ -1334,14 +1370,16 @@ __device__ __forceinline__ void d_scatter_list(const SysDev &s, const ListView &
                                                                 const u64 *rkey)
 {
     __shared__ i64 sm[32];
-    const i64 n = st->n_occ, m = st->n_keys, kn = st->kept_new;
+    const i64 n = st->n_occ;
     i64 asum = 0;
     unsigned err = 0;
     for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
         i64 v = wa.newpop[i];
         if (!(i == 0 || v != 0)) continue;
-        i64 ub = lower_bound_key(rkey, m, L.key[i]);
-        i64 out = wa.keep_l[i] + (ub < m ? wa.keep_s[ub] : kn);
+        // kept list entries before i, kept new keys before it (those inserted
+        // before earlier entries and those inserted right before i)
+        const i64 e = wa.keep_l[i];
+        const i64 out = (e & 0xFFFFFFFFLL) + (e >> 32) + wa.before[i];
         if (out >= O.cap) {
             err |= ERRB_LIST_OVERFLOW;
             continue;
@@ -1371,7 +1409,7 @@ __device__ __forceinline__ void d_scatter_new(const SysDev &s, const ListView &O
         i64 il = wa.ins[j];
         i64 v = rpop[j];
         if (il < 0 || v == 0) continue;
-        i64 out = wa.keep_s[j] + (il < n ? wa.keep_l[il] : kl);
+        i64 out = wa.keep_s[j] + (il < n ? (wa.keep_l[il] & 0xFFFFFFFFLL) : kl);
         if (out >= O.cap) {
             err |= ERRB_LIST_OVERFLOW;
             continue;
@@ -1424,6 +1462,7 @@ __device__ __forceinline__ void d_finalize(DevStep *st, const RunParams &p, cons
         r.n_keys = st->n_keys + st->n_hit;
         r.n_clusters = ncl;
         r.n_direct = st->n_direct;
+        st->prev_spawned = r.n_spawned;
         wa.ring[st->iter % RING] = r;
         st->n_start = st->n_occ;
         st->n_occ = r.nocc_after < list_cap ? r.nocc_after : list_cap;

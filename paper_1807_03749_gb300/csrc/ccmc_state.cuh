@@ -33,6 +33,8 @@ struct RunParams {
     int int_round;        // rounding decisions from the FP64 bit pattern (cutoff 0 or 2^k)
     int a_thresh_one;     // A_thresh == 1: floor(|A|) without a division
     int direct;           // spawns onto listed determinants are added to them directly (not sorted)
+    int nranks;           // simulated processors (Sec. III): composite clusters only from co-located excitors
+    int nu_move;          // owners move every 2^nu_move iterations (>= 64: never)
     i64 work_cap;         // samples, visit attempts or cluster attempts per step beyond which the step is abandoned
     RoundSpec spawn_rs;   // spawn rounding (with the cutoff)
     RoundSpec death_rs;   // death rounding (no cutoff)
@@ -85,6 +87,7 @@ struct DevStep {
     i64 nkb;            // key buckets in use (0: no direct accumulation this step)
     i64 n_direct;       // spawned records added directly to listed determinants
     i64 n_hit;          // listed determinants that received such records
+    i64 prev_spawned;   // spawned records of the previous step (0 after a list upload)
 };
 
 // Spawn buffer pair for the radix sort (ping-pong).
@@ -103,11 +106,25 @@ struct ClusterBuf {
     i64 cap;
 };
 
+// The cluster sampler's view of one list entry, written by the scans each
+// step and gathered by a pick in one place (32-byte sectors, 64 bytes for up
+// to four words): selection prefix, population, death factor, <HF|H|D> and
+// the bit string.
+template <int K>
+struct __align__(32) PickEntry {
+    i64 prefix;     // inclusive |pop| prefix over entries >= 1 (entry 0: 0)
+    i64 pop;
+    double tdeath;  // tau (Delta E_i - S): the death factor of this step
+    double href;    // <HF|H|D_i> (levels 1-2; 0 otherwise; 0 with full non-composite sampling)
+    u64 w[K];
+};
+
+static_assert(sizeof(PickEntry<2>) == 64 && sizeof(PickEntry<4>) == 64 && sizeof(PickEntry<6>) == 96,
+              "pick table rows: 64 bytes up to four words, 96 above");
+
 // Per-step work arrays over the list and the merge.
 struct WorkArrays {
-    i64 *prefix;      // inclusive |pop| prefix over entries >= 1 (entry 0: 0)
-    double *tdeath;   // tau (Delta E_i - S) per entry (the death factor of this step)
-    double *href;     // <HF|H|D_i> per entry (levels 1-2; 0 otherwise), without full non-composite sampling
+    void *picks;      // PickEntry<K>[list capacity]
     int *bucket;      // owner of the first position of each selection bucket
     int bucket_bits;  // log2 of the bucket capacity
     i64 *att_end;     // inclusive prefix of full non-composite attempts
@@ -120,7 +137,8 @@ struct WorkArrays {
     i64 *part;        // block partials of the scans (4 per block)
     u64 *enum_part;   // 128-bit fixed-point E_num partial (lo, hi) per producing block
     i64 *newpop;      // list values after the merge (threshold applied)
-    i64 *keep_l;      // keep flags of list entries -> exclusive prefix
+    i64 *keep_l;      // keep flag | before << 32 of list entries -> exclusive prefix (both counts)
+    int *before;      // kept new keys inserted just before each list entry
     i64 *keep_s;      // keep flags of reduced spawns -> exclusive prefix
     i64 *ins;         // insertion position of a new key, -1 when matched
     unsigned *hist;   // radix histograms, digit-major (2^bits x sort grid)

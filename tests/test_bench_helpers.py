@@ -91,3 +91,43 @@ def test_oracle_on_several_cores_small_workload():
     w = workload("ueg14_m38_ccsd")
     v, kps, cores, secs, rates, nslices, count = bench.oracle_all_cores(w, 0.3, cores=2, per_slice=2000)
     assert cores == 2 and v > 0 and secs > 0 and nslices >= 1 and kps >= 0 and count >= 1 and len(rates) == 2
+
+
+def test_summarize_ncu_per_unit_figures(tmp_path):
+    """The per-phase summary written from an ncu CSV of one step's kernels
+    and that step's record: bytes and instructions per unit, time-weighted
+    issue activity, lanes per instruction."""
+    import json
+
+    hdr = '"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size","Grid Size",' \
+          '"Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"\n'
+    rows = []
+
+    def add(kid, name, metric, unit, value):
+        rows.append(f'"{kid}","1","python","h","{name}","1","7","(256, 1, 1)","(1216, 1, 1)","0","10.3","",'
+                    f'"{metric}","{unit}","{value}"\n')
+
+    for kid, name, t, rd, wr, inst, tinst, issue in [
+            (0, "void ccmc::k_sample<2, double>(const ccmc::StepArgs *, int)", 2.0, 10.0, 2.0, 100.0, 1600.0, 50.0),
+            (1, "ccmc::k_sort_scatter(const ccmc::StepArgs *, int, int, int)", 1.0, 3.0, 3.0, 10.0, 320.0, 20.0),
+            (2, "ccmc::k_sort_hist(const ccmc::StepArgs *, int, int, int)", 1.0, 1.0, 0.0, 5.0, 160.0, 40.0)]:
+        add(kid, name, "gpu__time_duration.sum", "msecond", t)
+        add(kid, name, "dram__bytes_read.sum", "Mbyte", rd)
+        add(kid, name, "dram__bytes_write.sum", "Mbyte", wr)
+        add(kid, name, "smsp__inst_executed.sum", "inst", inst)
+        add(kid, name, "smsp__thread_inst_executed.sum", "inst", tinst)
+        add(kid, name, "smsp__issue_active.avg.pct_of_peak_sustained_active", "%", issue)
+    csvp = tmp_path / "l.csv"
+    csvp.write_text("==PROF== noise\n" + hdr + "".join(rows))
+    rec = dict(n_sel=1000, n_visit=0, n_attempts=900, n_spawned=400, n_direct=0, n_keys=50, nocc_after=300)
+    recp = tmp_path / "r.json"
+    recp.write_text(json.dumps([rec]))
+    out = tmp_path / "traffic_toy.txt"
+    bench.summarize_ncu(str(csvp), str(recp), str(out), "ncu ... python bench.py")
+    lines = [ln.split() for ln in out.read_text().splitlines() if not ln.startswith("#")]
+    got = {f[0]: f for f in lines}
+    assert got["sample"][1] == "k_sample" and got["sample"][2] == "sample"
+    assert float(got["sample"][3]) == 12e6 / 1000 and float(got["sample"][4]) == 1600.0 / 1000
+    assert float(got["sample"][6]) == 16.0
+    # the sort: two kernels summed, the longest named, issue weighted by time
+    assert float(got["sort"][3]) == 7e6 / 400 and abs(float(got["sort"][5]) - 30.0) < 1e-9

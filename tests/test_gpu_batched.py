@@ -121,3 +121,27 @@ def test_member_reads_wait_for_the_batch_stream():
         assert np.array_equal(x, y) and np.array_equal(x, z)
     assert a.records()[-1] == ref.records()[-1]
     b.close()
+
+
+def test_sixty_four_replicas_equal_plain():
+    """The full 64-replica recipe (every M x r_s x truncation combination) at
+    small targets: the batched step gives every replica the lists and records
+    it gets stepped alone."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA")
+    import paper_1807_03749_gb300 as ccmc
+
+    reps = [dict(w, target_pop=w["target_pop"] / 100.0, d0_init=20.0, list_capacity=0) for w in batched_replicas(64)]
+    stream = torch.cuda.Stream()
+    bctx = [ccmc.from_workload(w) for w in reps]
+    pctx = [ccmc.from_workload(w) for w in reps]
+    b = ccmc.Batch(bctx, stream.cuda_stream)
+    b.step(80)
+    for c in pctx:
+        c.step(80)
+    for cb, cp in zip(bctx, pctx):
+        assert cb.records() == cp.records()
+        for x, y in zip(cb.get_list(), cp.get_list()):
+            assert np.array_equal(x, y)
+    b.close()

@@ -49,7 +49,7 @@ def _pair(ccmc, w, **over):
     w.update(over)
     so = _oracle_system(w)
     keys = ("tau", "target_pop", "d0_init", "shift_a", "zeta", "spawn_cutoff", "fnc", "multispawn", "a_thresh",
-            "seed", "replica")
+            "seed", "replica", "n_ranks", "nu_move")
     sim = oracle.Sim(so, **{k: w[k] for k in keys if k in w})
     ctx = ccmc.from_workload(w)
     return so, sim, ctx
@@ -84,12 +84,15 @@ def _same_spawned(sim, ctx):
 
 def _run_lockstep(sim, ctx, nsteps, check_spawned_every=10):
     """Steps both sides together; records and lists must agree after every
-    step, spawned multisets every check_spawned_every steps (0: never)."""
+    step, spawned multisets every check_spawned_every steps (0: never).
+    Returns the GPU's records."""
+    grecs = []
     for k in range(nsteps):
         # death deltas belong to the list at the step start: take the oracle's before stepping
         rec = sim.step()
         ctx.step(1)
         grec = ctx.records()[-1]
+        grecs.append(grec)
         _same_record(rec, grec)
         if check_spawned_every and k % check_spawned_every == 0:
             gk, gp = ctx.get_spawned()
@@ -98,6 +101,7 @@ def _run_lockstep(sim, ctx, nsteps, check_spawned_every=10):
             b = np.lexsort((gp, gk))
             assert np.array_equal(ok_[a], gk[b]) and np.array_equal(op_[a], gp[b])
         _same_list(sim, ctx)
+    return grecs
 
 
 def test_ueg38_ccsd_full_run_bitexact(ccmc):
@@ -131,7 +135,7 @@ def test_ueg114_long_lockstep_and_determinism(ccmc):
     a second context with the same seed reproducing the run exactly."""
     w = workload("ueg14_m114_ccsdt_fnc_ms")
     so, sim, ctx = _pair(ccmc, w)
-    twin = ccmc.from_workload(w)
+    twin = ccmc.from_workload(w, sort_all=True)
     for k in range(600):
         rec = sim.step()
         ctx.step(1)
@@ -197,7 +201,8 @@ def test_ueg114_full_size_step_bitexact(ccmc):
         _same_list(sim, ctx)
 
 
-def test_molecule_full_size_step_bitexact(ccmc):
+@pytest.mark.parametrize("multispawn", [False, True])
+def test_molecule_full_size_step_bitexact(ccmc, multispawn):
     """The synthetic molecule (20 electrons, 82 spin-orbitals, CCSDTQ, two-word
     determinants) at full size: about 4e6 occupied excitors of levels 0-4 and
     N_total of about 1.2e7, one step in the production launch configuration.
@@ -206,7 +211,7 @@ def test_molecule_full_size_step_bitexact(ccmc):
     merged list and the record must match."""
     from ccmc_inputs import molecule_state
 
-    w = workload("mol20_m82_ccsdtq", tau=0.005)
+    w = workload("mol20_m82_ccsdtq", tau=0.005, multispawn=multispawn)
     h1, eri = molecule_integrals(norb=41, nocc=10, seed=7)
     w.update(h1=h1, eri=eri, nso=82)
     so, sim, ctx = _pair(ccmc, w)
@@ -224,6 +229,32 @@ def test_molecule_full_size_step_bitexact(ccmc):
     _same_list(sim, ctx)
 
 
+def test_molecule_grown_state_step_bitexact(ccmc):
+    """The benchmark's own molecule state: grown on the GPU from the reference
+    (tau = 2e-6, target 10^7) until the shift has varied for 400 steps, about
+    1.8e7 occupied excitors and N_total = 2.3e7; the next step of GPU and
+    oracle from that state agree bit for bit (records and list)."""
+    w = workload("mol20_m82_ccsdtq")
+    h1, eri = molecule_integrals(norb=41, nocc=10, seed=7)
+    w.update(h1=h1, eri=eri, nso=82)
+    so, sim, ctx = _pair(ccmc, w, sort_all=False)
+    for _ in range(200):
+        ctx.step(10)
+        if ctx.get_state()[2]:
+            break
+    ctx.step(400)
+    bits, _, pop = ctx.get_list()
+    it, shift, vary, nprev = ctx.get_state()
+    assert vary and len(pop) > 10_000_000
+    sim.set_list_words(bits, pop)
+    sim.set_state(it, shift, bool(vary), nprev)
+    ctx.records()
+    rec = sim.step()
+    ctx.step(1)
+    _same_record(rec, ctx.records()[-1])
+    _same_list(sim, ctx)
+
+
 @pytest.mark.parametrize("sort_all", [True, False])
 def test_molecule_all_samplers_bitexact(ccmc, sort_all):
     """A small molecule-like Hamiltonian (singles exist, so composite clusters
@@ -235,31 +266,39 @@ def test_molecule_all_samplers_bitexact(ccmc, sort_all):
     for fnc, ms in [(0, 0), (1, 0), (0, 1), (1, 1)]:
         w = dict(base, fnc=fnc, multispawn=ms)
         so, sim, ctx = _pair(ccmc, w, sort_all=sort_all)
-        _run_lockstep(sim, ctx, 80, check_spawned_every=20 if sort_all else 0)
+        grecs = _run_lockstep(sim, ctx, 80, check_spawned_every=20 if sort_all else 0)
         if not sort_all:
-            assert sum(r["n_direct"] for r in ctx.records()) > 0
+            assert sum(r["n_direct"] for r in grecs) > 0
         ctx.close()
 
 
 def test_direct_accumulation_lockstep_ueg114(ccmc):
     """The annihilation fast path (records onto listed determinants added with
     integer atomics, only new keys sorted) on the 114 spin-orbital FNC +
-    multi-spawn run: 300 steps in lockstep with the oracle, records and lists
-    bit for bit; most records take the fast path once the list has grown."""
+    multi-spawn run at its working population: the GPU grows the run from the
+    reference to 10^6 (the path switches itself on once a step spawns more
+    than a tenth of the list's size in records), then 40 steps in lockstep
+    with the oracle from the GPU's state, records and lists bit for bit, most
+    records on the fast path."""
     w = workload("ueg14_m114_ccsdt_fnc_ms")
-    so, sim, ctx = _pair(ccmc, w, sort_all=False)
+    so, sim, _ = _pair(ccmc, w)
+    ctx = ccmc.from_workload(w)
+    ctx.step(1500)
+    bits, _, pop = ctx.get_list()
+    it, shift, vary, nprev = ctx.get_state()
+    sim.set_list_words(bits, pop)
+    sim.set_state(it, shift, bool(vary), nprev)
+    ctx.records()
     direct = total = 0
-    for k in range(300):
+    for k in range(40):
         rec = sim.step()
         ctx.step(1)
         g = ctx.records()[-1]
         _same_record(rec, g)
         direct += g["n_direct"]
         total += g["n_spawned"]
-        if k % 25 == 0:
-            _same_list(sim, ctx)
     _same_list(sim, ctx)
-    assert 0 < direct < total and direct > total // 2
+    assert direct > total // 2
 
 
 def test_direct_accumulation_fp32_gas_at_scale(ccmc):
@@ -303,6 +342,35 @@ def test_six_word_determinants_bitexact(ccmc):
     so, sim, ctx = _pair(ccmc, w)
     _run_lockstep(sim, ctx, 30, check_spawned_every=5)
     assert len(ctx.get_list()[1]) > 1000
+
+
+def test_distributed_sampling_bitexact(ccmc):
+    """The simulated distribution over processors (Sec. III, Eq. ccmc_dist):
+    8 processors, owners moving every 4 iterations, on the 66 spin-orbital
+    CCSDT gas with full non-composite sampling and multi-spawn, in lockstep
+    with the oracle."""
+    w = workload("ueg14_m66_ccsdt_rs5", target_pop=2e4, d0_init=300.0, multispawn=True, n_ranks=8, nu_move=2)
+    so, sim, ctx = _pair(ccmc, w)
+    _run_lockstep(sim, ctx, 120, check_spawned_every=20)
+    # the restriction is active: the same run on one processor differs
+    so1, sim1, ctx1 = _pair(ccmc, dict(w, n_ranks=1))
+    for _ in range(120):
+        ctx1.step(1)
+    assert not np.array_equal(ctx1.get_list()[2], ctx.get_list()[2])
+
+
+def test_colocation_matches_oracle(ccmc):
+    """Pair co-location sums of Fig. excitdistrib on the 3,813 excitors of the
+    14-electron, 186 spin-orbital CCSD space: GPU and oracle agree exactly."""
+    so = oracle.System.ueg(14, 186, 1.0, 2)
+    keys = so.space_keys(2, expand_top=False)
+    dets = np.stack([so.to_words(so.unrank(int(k))) for k in keys])
+    assert len(dets) == 3813     # the paper's 3,813 (the reference included)
+    ck = [1, 5, 16, 48]
+    for np_, nu in ((32, 4), (7, 0)):
+        g1, g2 = ccmc.colocation(dets, np_, nu, ck)
+        o1, o2 = oracle.colocation(dets, np_, nu, ck)
+        assert np.array_equal(g1, o1) and np.array_equal(g2, o2)
 
 
 def test_fp32_form_ueg38_bitexact(ccmc):
