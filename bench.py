@@ -260,6 +260,20 @@ def summarize_ncu(csv_path: str, records_path: str, out_path: str, command: str)
             lanes = a["tinst"] / a["inst"] if a["inst"] else 0.0
             f.write(f"{ph:9s} {a['top'][1]:18s} {UNIT_OF_PHASE[ph]:8s} {a['dram'] / u:14.3f} {a['tinst'] / u:14.3f} "
                     f"{issue:6.1f} {lanes:6.2f}\n")
+        # the launch list of the captured step: per kernel its launches, total
+        # time (serialised and cold-cache under ncu: compare shares), share,
+        # DRAM bytes per launch
+        kern = {}
+        for (kid, name), m in rows.items():
+            short = name.split("(")[0].replace("ccmc::", "").replace("void ", "").strip()
+            k = kern.setdefault(short, [0, 0.0, 0.0])
+            k[0] += 1
+            k[1] += m.get("gpu__time_duration.sum", 0.0)
+            k[2] += m.get("dram__bytes_read.sum", 0.0) + m.get("dram__bytes_write.sum", 0.0)
+        tot = sum(v[1] for v in kern.values()) or 1.0
+        f.write("# launch list of the captured step (kernel, launches, total us, share, DRAM MB per launch):\n")
+        for name, (nl, t, b) in sorted(kern.items(), key=lambda kv: -kv[1][1]):
+            f.write(f"#   {name:34s} {nl:4d} {t * 1e6:12.1f} {100.0 * t / tot:6.1f}% {b / nl / 1e6:10.2f}\n")
 
 
 def roofline_objects(name: str, pms: dict, nprof: int, precs_by_ctx: list, nw_by_ctx: list, lmax_by_ctx: list,

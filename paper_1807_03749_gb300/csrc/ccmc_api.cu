@@ -347,19 +347,23 @@ cudaError_t load_list(ccmc_ctx *ctx, ListView &L, i64 n)
     const int g = (int)std::min<i64>(4096, (n + 255) / 256 + 1);
     const bool f = ctx->sc.fp32;
     cudaStream_t sm = ctx->stream;
+    const SysDev &s = ctx->sc.sys;
     switch (ctx->sc.K) {
     case 1:
-        if (f) k_load_list<1, float><<<g, 256, 0, sm>>>(ctx->sc.sys, L, ctx->io, n, ctx->d_bad);
-        else k_load_list<1, double><<<g, 256, 0, sm>>>(ctx->sc.sys, L, ctx->io, n, ctx->d_bad);
+        if (f) k_load_list<1, float><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad);
+        else k_load_list<1, double><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad);
         break;
     case 2:
-        if (f) k_load_list<2, float><<<g, 256, 0, sm>>>(ctx->sc.sys, L, ctx->io, n, ctx->d_bad);
-        else k_load_list<2, double><<<g, 256, 0, sm>>>(ctx->sc.sys, L, ctx->io, n, ctx->d_bad);
+        if (f) k_load_list<2, float><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad);
+        else k_load_list<2, double><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad);
         break;
-    default:
-        if (f) k_load_list<3, float><<<g, 256, 0, sm>>>(ctx->sc.sys, L, ctx->io, n, ctx->d_bad);
-        else k_load_list<3, double><<<g, 256, 0, sm>>>(ctx->sc.sys, L, ctx->io, n, ctx->d_bad);
+    case 3:
+        if (f) k_load_list<3, float><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad);
+        else k_load_list<3, double><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad);
         break;
+    case 4: k_load_list<4, double><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad); break;   // FP64 only
+    case 5: k_load_list<5, double><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad); break;
+    default: k_load_list<6, double><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad); break;
     }
     k_check_order<<<g, 256, 0, sm>>>(L.key, n, ctx->d_bad);
     return cudaGetLastError();
@@ -371,7 +375,10 @@ cudaError_t store_list(ccmc_ctx *ctx, const ListView &L, i64 n)
     switch (ctx->sc.K) {
     case 1: k_store_list<1><<<g, 256, 0, ctx->stream>>>(L, ctx->io, n); break;
     case 2: k_store_list<2><<<g, 256, 0, ctx->stream>>>(L, ctx->io, n); break;
-    default: k_store_list<3><<<g, 256, 0, ctx->stream>>>(L, ctx->io, n); break;
+    case 3: k_store_list<3><<<g, 256, 0, ctx->stream>>>(L, ctx->io, n); break;
+    case 4: k_store_list<4><<<g, 256, 0, ctx->stream>>>(L, ctx->io, n); break;
+    case 5: k_store_list<5><<<g, 256, 0, ctx->stream>>>(L, ctx->io, n); break;
+    default: k_store_list<6><<<g, 256, 0, ctx->stream>>>(L, ctx->io, n); break;
     }
     return cudaGetLastError();
 }
@@ -473,7 +480,11 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     // spawned records per step: about one per attempt; multi-spawn makes several attempts per cluster
     const double per = params->multispawn ? 8.0 : (params->fnc ? 3.0 : 2.0);
     ctx->spawn_cap = params->spawn_capacity ? (i64)params->spawn_capacity : (i64)(per * tgt + 65536.0);
-    ctx->cl_cap = params->multispawn ? (i64)(3.0 * tgt + 65536.0) : 1;
+    // the original sampler on a generic Hamiltonian queues its clusters for
+    // the attempts kernel (their attempts are long and divergent); the
+    // trajectory is the same either way
+    const bool buffered = !params->multispawn && ham->kind == CCMC_GENERIC;
+    ctx->cl_cap = params->multispawn ? (i64)(3.0 * tgt + 65536.0) : (buffered ? (i64)(4.0 * tgt + 65536.0) : 1);
     if (ctx->list_cap < 2 || ctx->spawn_cap < 1 || ctx->spawn_cap >= (i64)0xFFFFFFFFLL) {
         delete ctx;
         return CCMC_ERR_ARG;
@@ -561,6 +572,7 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     rp.replica = params->replica;
     rp.fnc = params->fnc ? 1 : 0;
     rp.multispawn = params->multispawn ? 1 : 0;
+    rp.buffered = buffered ? 1 : 0;
     rp.a_thresh_one = params->a_thresh == 1.0 ? 1 : 0;
     rp.direct = (params->flags & CCMC_SORT_ALL) ? 0 : 1;
     rp.nranks = params->n_ranks > 1 ? params->n_ranks : 1;
@@ -1315,7 +1327,7 @@ ccmc_status ccmc_batch_create(ccmc_ctx **ctxs, int32_t n, void *cuda_stream, ccm
             delete b;
             return CCMC_ERR_CUDA;
         }
-        bool multi = c->prm.fnc || c->prm.multispawn;
+        bool multi = c->prm.fnc || c->prm.multispawn || c->sc.prm.buffered;
         bool fp32 = c->sc.fp32;
         BatchGroup *g = nullptr;
         for (BatchGroup &x : b->groups)

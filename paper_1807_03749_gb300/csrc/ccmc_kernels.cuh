@@ -311,7 +311,9 @@ __device__ __forceinline__ void window_step(const i64 *end, i64 n, i64 t0, Attem
     i64 before = __shfl_sync(FULLMASK, ev, L > 0 ? L - 1 : 0);
     owner = w.cur + L;
     m = t - (L > 0 ? before : w.prev);
-    unsigned done = __ballot_sync(FULLMASK, ev <= t0 + 31);
+    // entries whose attempts all lie before t0 + 32 are finished; the next
+    // window starts at the owner of attempt t0 + 32
+    unsigned done = __ballot_sync(FULLMASK, ev <= t0 + 32);
     int adv = __popc(done);
     if (adv > 0) w.prev = __shfl_sync(FULLMASK, ev, adv - 1);
     w.cur += adv;
@@ -912,7 +914,10 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
                 }
                 natt = snatt[sz];   // = attempts_of(|amp|): |amp| = mag[sz] for every cluster of size sz
                 valid_cl = true;
-                if (p.multispawn) {
+                if (p.buffered) {
+                    catt = coef;    // the original sampler's one attempt
+                    cl_att += 1;
+                } else if (p.multispawn) {
                     // coef / natt: the same division, done once per size
                     catt = natt > 1 ? (coef < 0.0 ? -scmag[sz] : scmag[sz]) : coef;
                     if (natt > p.work_cap) {   // runaway: the attempts kernel will not run them
@@ -925,17 +930,19 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
         }
         rec_push(rb, rn, rec, rk, rv);
         rec_flush(rb, rn, false, st, sp, dv, ndirect, err);   // the stage holds fewer than 32 again
-        if (p.multispawn) {
-            u64 mine = valid_cl ? ((1ULL << CL_SHIFT) | (u64)natt) : 0ULL;
+        if (p.multispawn || p.buffered) {
+            // the cluster is queued for the attempts kernel: multi-spawn
+            // packs (clusters << CL_SHIFT | attempts) into one counter; the
+            // original sampler's one attempt per cluster counts clusters only
+            u64 mine = valid_cl ? (p.buffered ? 1ULL : ((1ULL << CL_SHIFT) | (u64)natt)) : 0ULL;
             u64 o = warp_reserve_u64(&st->cl_packed, mine);
             if (valid_cl) {
-                i64 c = (i64)(o >> CL_SHIFT);
-                i64 a0 = (i64)(o & CL_MASK);
+                const i64 c = p.buffered ? (i64)o : (i64)(o >> CL_SHIFT);
                 if (c < cl.cap) {
                     store_det<K>(cl.bits, cl.cap, c, dj);
                     cl.catt[c] = catt;
                     cl.index[c] = (u64)g;
-                    cl.end[c] = a0 + natt;
+                    cl.end[c] = p.buffered ? c + 1 : (i64)(o & CL_MASK) + natt;
                 } else {
                     err |= ERRB_CLUSTER_OVERFLOW;
                 }
@@ -965,7 +972,7 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
     inline_att = block_sum(inline_att, sm);
     death_hf = block_sum(death_hf, sm);
     ndirect = block_sum(ndirect, sm);
-    if (p.multispawn) {
+    if (p.multispawn || p.buffered) {
         __shared__ double smd[32];
         double ca = block_sum((double)cl_att, smd);
         if (threadIdx.x == 0 && ca != 0.0) atomicAdd(&st->cl_att, ca);
@@ -996,7 +1003,7 @@ __device__ __forceinline__ void d_attempts(const SysDev &s, const ListView &L, D
         return;
     }
     const i64 n = st->n_occ, tf = st->fnc_attempts;
-    i64 ncl = (i64)(st->cl_packed >> CL_SHIFT);
+    i64 ncl = p.buffered ? (i64)st->cl_packed : (i64)(st->cl_packed >> CL_SHIFT);
     if (ncl > cl.cap) ncl = cl.cap;
     const i64 tc = ncl > 0 ? cl.end[ncl - 1] : 0;
     const u64 it = st->iter;
@@ -1444,7 +1451,7 @@ __device__ __forceinline__ void d_finalize(DevStep *st, const RunParams &p, cons
     }
     k = block_fix(k, smf);
     if (threadIdx.x == 0) {
-        i64 ncl = (i64)(st->cl_packed >> CL_SHIFT);
+        i64 ncl = p.buffered ? (i64)st->cl_packed : (i64)(st->cl_packed >> CL_SHIFT);
         if (ncl > cl.cap) ncl = cl.cap;
         i64 tc = ncl > 0 ? cl.end[ncl - 1] : 0;
         Record r;

@@ -33,6 +33,7 @@ struct RunParams {
     int int_round;        // rounding decisions from the FP64 bit pattern (cutoff 0 or 2^k)
     int a_thresh_one;     // A_thresh == 1: floor(|A|) without a division
     int direct;           // spawns onto listed determinants are added to them directly (not sorted)
+    int buffered;         // original sampler: each valid cluster's one attempt runs in the attempts kernel
     int nranks;           // simulated processors (Sec. III): composite clusters only from co-located excitors
     int nu_move;          // owners move every 2^nu_move iterations (>= 64: never)
     i64 work_cap;         // samples, visit attempts or cluster attempts per step beyond which the step is abandoned

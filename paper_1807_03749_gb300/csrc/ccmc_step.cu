@@ -236,7 +236,7 @@ cudaError_t launch_group(const StepArgs *A, int nrep, int K, bool fp32, const Sh
 
 cudaError_t launch_step(StepCtx &c)
 {
-    cudaError_t e = launch_group(c.d_args, 1, c.K, c.fp32, c.sh, c.prm.fnc || c.prm.multispawn, c.stream, c.launches,
+    cudaError_t e = launch_group(c.d_args, 1, c.K, c.fp32, c.sh, c.prm.fnc || c.prm.multispawn || c.prm.buffered, c.stream, c.launches,
                                  c.profile ? c.events : nullptr);
     c.sorted_buf = sort_passes(c.sh) & 1;
     c.cur ^= 1;
