@@ -17,7 +17,7 @@ composite clusters are formed only from excitors on one simulated processor,
 for several N_p, against N_p = 1 (no bias).
 
     python distribution.py colocation
-    python distribution.py bias --ranks 1,8,32,96,240 --steps 20000
+    python distribution.py bias --ranks 1,8,32,96,240 --steps 100000
 """
 from __future__ import annotations
 
@@ -95,33 +95,40 @@ def run_bias(args):
             stream = torch.cuda.Stream()
             ctx = ccmc.from_workload(w, stream=stream.cuda_stream)
             t0 = time.perf_counter()
-            grown, reached = 0, None
-            while grown < 100000:
-                ctx.step(w["shift_a"])
-                grown += w["shift_a"]
-                if reached is None and ctx.get_state()[2]:
-                    reached = grown
-                if reached is not None and grown >= reached + args.equilibrate:
-                    break
-            ctx.records()
-            recs = []
-            while len(recs) < args.steps:
-                ctx.step(100)
-                recs += ctx.records()
+            grown, reached, recs, status = 0, None, [], "ok"
+            try:
+                while grown < args.grow_max:
+                    ctx.step(w["shift_a"])
+                    grown += w["shift_a"]
+                    if reached is None and ctx.get_state()[2]:
+                        reached = grown
+                    if reached is not None and grown >= reached + args.equilibrate:
+                        break
+                ctx.records()
+                while reached is not None and len(recs) < args.steps:
+                    ctx.step(100)
+                    recs += ctx.records()
+            except ccmc.CCMCError as e:   # a runaway population ends the run
+                status = str(e).split(":")[0]
+            ctx.close()
+            row = {"system": rs_name, "n_ranks": np_, "nu_move": args.nu_move, "tau": args.tau, "status": status,
+                   "steps": len(recs), "seconds": time.perf_counter() - t0}
+            if status != "ok" or len(recs) < 1000:
+                row["status"] = status if status != "ok" else "shift never started to vary"
+                results.append(row)
+                print(json.dumps(row), flush=True)
+                continue
             e, se, es, ses = energy.projected_energy(recs)
             n0 = sum(r["n0"] for r in recs) / len(recs) / 65536.0
             nt = sum(r["ntot_after"] for r in recs) / len(recs) / 65536.0
-            row = {"system": rs_name, "n_ranks": np_, "nu_move": args.nu_move, "tau": args.tau, "e_proj": e,
-                   "e_proj_err": se, "reference_fraction": n0 / nt, "n_occ": recs[-1]["nocc_after"],
-                   "excitors_per_rank": recs[-1]["nocc_after"] / np_, "steps": len(recs),
-                   "seconds": time.perf_counter() - t0}
+            row.update(e_proj=e, e_proj_err=se, reference_fraction=n0 / nt, n_occ=recs[-1]["nocc_after"],
+                       excitors_per_rank=recs[-1]["nocc_after"] / np_)
             if base is None:
                 base = (e, se)
             row["bias"] = e - base[0]
             row["bias_err"] = math.sqrt(se ** 2 + base[1] ** 2)
             results.append(row)
             print(json.dumps(row), flush=True)
-            ctx.close()
     print(json.dumps({"bias": results}), flush=True)
 
 
@@ -138,7 +145,8 @@ def main():
     ap.add_argument("--tau", type=float, default=0.001)
     ap.add_argument("--target-pop", type=float, default=2e5)
     ap.add_argument("--equilibrate", type=int, default=2000)
-    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--steps", type=int, default=100000)
+    ap.add_argument("--grow-max", type=int, default=20000, help="growth steps before giving up on the shift")
     args = ap.parse_args()
     if args.mode == "colocation":
         run_colocation(args)

@@ -338,12 +338,16 @@ ccmc_status ccmc_reduce_records_noalloc(const uint64_t *keys_in, const int64_t *
  * each processor forms composite clusters only from its own excitors.  Here
  * the hash is Philox-4x64-10 under a fixed key used as a mixing function over
  * the bit string (three words per call, each call chained through the fourth
- * counter word).  With ccmc_params.n_ranks = N_p > 1 the step keeps a
- * composite cluster of size s only if all its excitors have the same owner at
- * the current iteration, and multiplies its amplitude by N_p^(s-1) (the
- * inverse of the co-location probability), so that the step is unbiased
- * averaged over owners while each iteration samples a subspace -- the source
- * of the parallelisation bias the paper studies.
+ * counter word).  With ccmc_params.n_ranks = N_p > 1 (at most 65535) a
+ * composite cluster of size s is drawn as a processor would draw it from the
+ * excitors it holds: its first excitor from the whole list (a processor
+ * samples in proportion to its population), the others from the first one's
+ * processor q only, in proportion to |t| among q's excitors (N_q their sum).
+ * Its amplitude is N_ex (N_q N_p)^(s-1) / (|t_HF|^(s-1) n_sel p(s) s!): the
+ * inverse selection probability times N_p^(s-1), the inverse of the
+ * probability that s excitors share a processor, so that the step is
+ * unbiased averaged over owners while each iteration samples a subspace --
+ * the source of the parallelisation bias the paper studies.
  *
  * ccmc_colocation computes the co-location statistics of Fig. excitdistrib
  * for n determinants (host array, n rows of n_words words): for every

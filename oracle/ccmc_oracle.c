@@ -24,6 +24,8 @@
  *   Sec. II                 shift held then varied to keep the population stable
  *   Sec. IV.B               full non-composite (FNC) sampling
  *   Sec. IV.C, Eq. 7-8      multi-spawn: n_attempts = max(1, floor(A/A_thresh))
+ *   Sec. III, Eq. ccmc_dist simulated distribution over N_p processors: owner
+ *                           hash; composite clusters from one processor's excitors
  *
  * Diagonal energies H_DD - E_HF use the excitation form (reference Fock
  * diagonal plus pair corrections among holes and particles), pinned against
@@ -1146,9 +1148,62 @@ static int64_t pick_index(const int64_t *prefix, int64_t n, uint64_t x)
     return lo;
 }
 
+/* Simulated distribution (Sec. III): a processor forms composite clusters
+ * only from the excitors it holds.  The excitors (entries i >= 1) grouped by
+ * their owner at this iteration, ascending within each group, with running
+ * sums of |t_i| per group; N_q is processor q's total. */
+typedef struct {
+    int64_t *own, *start, *count, *order, *lpre, *nq;
+} orc_local;
+
+static void local_free(orc_local *l)
+{
+    free(l->own); free(l->start); free(l->count); free(l->order); free(l->lpre); free(l->nq);
+}
+
+static int local_build(const orc_sim *m, orc_local *l)
+{
+    const int64_t n = m->n, np_ = m->prm.n_ranks;
+    l->own = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    l->order = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    l->lpre = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    l->start = (int64_t *)calloc((size_t)np_, sizeof(int64_t));
+    l->count = (int64_t *)calloc((size_t)np_, sizeof(int64_t));
+    l->nq = (int64_t *)calloc((size_t)np_, sizeof(int64_t));
+    if (!l->own || !l->order || !l->lpre || !l->start || !l->count || !l->nq) return ORC_ERR_OOM;
+    for (int64_t i = 1; i < n; i++) {
+        l->own[i] = (int64_t)orc_owner(m->bits[i].w, m->sys->nw, m->iter, m->prm.nu_move, (uint64_t)np_);
+        l->count[l->own[i]]++;
+    }
+    for (int64_t q = 1; q < np_; q++) l->start[q] = l->start[q - 1] + l->count[q - 1];
+    int64_t *fill = (int64_t *)calloc((size_t)np_, sizeof(int64_t));
+    if (!fill) return ORC_ERR_OOM;
+    for (int64_t i = 1; i < n; i++) {
+        const int64_t q = l->own[i], k = l->start[q] + fill[q]++;
+        const int64_t a = m->pop[i] < 0 ? -m->pop[i] : m->pop[i];
+        l->order[k] = i;
+        l->nq[q] += a;
+        l->lpre[k] = l->nq[q];
+    }
+    free(fill);
+    return 0;
+}
+
+/* The excitor of processor q holding position x in [0, N_q): the first in
+ * the group whose running sum exceeds x. */
+static int64_t local_pick(const orc_local *l, int64_t q, uint64_t x)
+{
+    int64_t lo = l->start[q], hi = l->start[q] + l->count[q] - 1;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if ((uint64_t)l->lpre[mid] > x) hi = mid; else lo = mid + 1;
+    }
+    return l->order[lo];
+}
+
 /* Cluster sample g (Sec. II; FNC composites per Sec. IV.B). */
 static int sample_cluster(orc_sim *m, uint64_t g, const int64_t *prefix, int64_t nex,
-                          const double *mag, int fnc)
+                          const double *mag, const double *den, const orc_local *loc, int fnc)
 {
     const orc_system *s = m->sys;
     const uint64_t pkey[2] = { m->prm.seed, m->prm.replica };
@@ -1174,23 +1229,35 @@ static int sample_cluster(orc_sim *m, uint64_t g, const int64_t *prefix, int64_t
         if (sz >= 2 && n0 == 0) return 0;
         det_t ex[8];
         int neg = 0;
+        /* simulated distribution (Sec. III): the first excitor is drawn from
+           the whole list (a processor draws in proportion to the population
+           it holds), the others from the first one's processor q only */
+        const int local = loc && sz >= 2;
+        int64_t q = 0;
         for (int e = 0; e < sz; e++) {
-            uint64_t x = below(r[2 + e], (uint64_t)nex);
-            idx[e] = pick_index(prefix, m->n, x);
+            if (local && e >= 1) {
+                idx[e] = local_pick(loc, q, below(r[2 + e], (uint64_t)loc->nq[q]));
+            } else {
+                idx[e] = pick_index(prefix, m->n, below(r[2 + e], (uint64_t)nex));
+                if (local) q = loc->own[idx[0]];
+            }
             for (int f = 0; f < e; f++) if (idx[f] == idx[e]) return 0;   /* repeated excitor */
             ex[e] = m->bits[idx[e]];
             if (m->pop[idx[e]] < 0) neg ^= 1;
         }
-        /* simulated distribution (Sec. III): a composite cluster is formed
-           only from excitors on one processor at this iteration */
-        if (sz >= 2 && m->prm.n_ranks > 1) {
-            uint64_t own0 = orc_owner(ex[0].w, s->nw, m->iter, m->prm.nu_move, (uint64_t)m->prm.n_ranks);
-            for (int e = 1; e < sz; e++)
-                if (orc_owner(ex[e].w, s->nw, m->iter, m->prm.nu_move, (uint64_t)m->prm.n_ranks) != own0) return 0;
-        }
         if (!collapse(s, sz, ex, &dj, &sigma)) return 0;
         if (n0 < 0 && ((sz - 1) & 1)) neg ^= 1;
-        amp = neg ? -mag[sz] : mag[sz];
+        double a = mag[sz];
+        if (local) {
+            /* |A| = N_ex (N_q N_p)^(s-1) / (|t_HF|^(s-1) n_sel p(s) s!): the
+               selection probability p(s) s! prod|t| / (N_ex N_q^(s-1)) times
+               the co-location probability N_p^-(s-1) of the cluster */
+            const double f = ((double)loc->nq[q] / FIX_ONE) * (double)m->prm.n_ranks;
+            double num = (double)nex / FIX_ONE;
+            for (int e = 1; e < sz; e++) num = num * f;
+            a = num / den[sz];
+        }
+        amp = neg ? -a : a;
     }
     int lev = level_of(s, &dj);
     if (lev > s->lmax + 2) return 0;
@@ -1354,7 +1421,7 @@ static int sim_step_range(orc_sim *m, int propagate_only, int64_t i_lo, int64_t 
     m->rec.ntot = ntot;
     m->rec.n_sel = n_sel;
     /* |A| of a cluster of size s: N_ex^s / (|t_HF|^(s-1) n_sel p(s) s!) */
-    double mag[8] = { 0 };
+    double mag[8] = { 0 }, den_s[8] = { 0 };
     double nex_d = (double)nex / FIX_ONE;
     double n0_d = (double)(n0 < 0 ? -n0 : n0) / FIX_ONE;
     int smax = s->lmax + 2;
@@ -1376,15 +1443,14 @@ static int sim_step_range(orc_sim *m, int propagate_only, int64_t i_lo, int64_t 
         den = den * p;
         den = den * fact;
         mag[sz] = num / den;
-        /* with N_p simulated processors a composite cluster is co-located
-           with probability N_p^-(s-1): its amplitude carries N_p^(s-1) */
-        if (sz >= 2 && m->prm.n_ranks > 1) {
-            double f = 1.0;
-            for (int e = 1; e < sz; e++) f = f * (double)m->prm.n_ranks;
-            mag[sz] = mag[sz] * f;
-        }
+        den_s[sz] = den;
     }
+    orc_local loc = { 0 };
     int rc = 0;
+    if (m->prm.n_ranks > 1) {
+        rc = local_build(m, &loc);
+        if (rc) { local_free(&loc); free(prefix); return rc; }
+    }
     if (m->prm.fnc) {
         int64_t hi = i_hi < n ? i_hi : n;
         m->rec.n_visit = hi > i_lo ? hi - i_lo : 0;
@@ -1392,8 +1458,10 @@ static int sim_step_range(orc_sim *m, int propagate_only, int64_t i_lo, int64_t 
     }
     {
         int64_t hi = g_hi < n_sel ? g_hi : n_sel;
-        for (int64_t g = g_lo; g < hi && !rc; g++) rc = sample_cluster(m, (uint64_t)g, prefix, nex, mag, m->prm.fnc);
+        for (int64_t g = g_lo; g < hi && !rc; g++)
+            rc = sample_cluster(m, (uint64_t)g, prefix, nex, mag, den_s, m->prm.n_ranks > 1 ? &loc : NULL, m->prm.fnc);
     }
+    local_free(&loc);
     free(prefix);
     if (rc) return rc;
     m->rec.n_spawned = m->nsp;

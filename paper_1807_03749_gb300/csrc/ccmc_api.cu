@@ -402,7 +402,7 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     if (params->radix_bits < 0 || params->radix_bits > MAX_DIGIT_BITS) return CCMC_ERR_ARG;
     if (params->precision != CCMC_FP64 && params->precision != CCMC_FP32) return CCMC_ERR_ARG;
     if (params->precision == CCMC_FP32 && nso > 192) return CCMC_ERR_ARG;   // FP32 form: up to three words
-    if (params->n_ranks < 0 || params->nu_move < 0) return CCMC_ERR_ARG;
+    if (params->n_ranks < 0 || params->n_ranks > 65535 || params->nu_move < 0) return CCMC_ERR_ARG;
 
     ccmc_ctx *ctx = new (std::nothrow) ccmc_ctx();
     if (!ctx) return CCMC_ERR_OOM;
@@ -613,6 +613,7 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     sh.key_bits = bits_for(key_bound);
     sh.digit_bits = params->radix_bits ? params->radix_bits : MAX_DIGIT_BITS;
     sh.enum_slots = sh.scan_grid + sh.work_grid;
+    sh.nranks = rp.nranks;
     ctx->sc.K = h.nw;
     ctx->sc.fp32 = params->precision == CCMC_FP32;
 
@@ -640,11 +641,7 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     cl.end = al.arr<i64>(cl.cap);
     WorkArrays &wa = ctx->sc.wa;
     const i64 lc = ctx->list_cap;
-    {
-        // PickEntry<K> is 64 bytes for up to four words, 96 above
-        const size_t pe = K <= 4 ? 64 : 96;
-        wa.picks = al.get((size_t)lc * pe);
-    }
+    wa.picks = al.arr<PickEntry>(lc);
     wa.bucket_bits = 10;
     while (wa.bucket_bits < 22 && (1LL << wa.bucket_bits) < lc / 2) wa.bucket_bits++;
     wa.bucket = al.arr<int>(((size_t)1 << wa.bucket_bits) + 1);
@@ -666,6 +663,19 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     wa.hist = al.arr<unsigned>((size_t)(1 << MAX_DIGIT_BITS) * sh.sort_grid);
     wa.hist_tot = al.arr<unsigned>((size_t)(1 << MAX_DIGIT_BITS));
     wa.ring = al.arr<Record>(RING);
+    wa.owner = nullptr;
+    wa.lcp = nullptr;
+    wa.nq = nullptr;
+    wa.lcp_cap = 0;
+    if (rp.nranks > 1) {
+        // per-processor position table: chunks of at least 32 entries, at
+        // most 2^22 cells (chunks grow with the list beyond that)
+        const i64 want = (i64)rp.nranks * ((lc + 31) / 32);
+        wa.lcp_cap = std::max<i64>((i64)rp.nranks, std::min<i64>(want, 1LL << 22));
+        wa.owner = al.arr<unsigned short>(lc);
+        wa.lcp = al.arr<i64>(wa.lcp_cap);
+        wa.nq = al.arr<i64>(rp.nranks);
+    }
     ctx->io = al.arr<u64>((size_t)K * (size_t)lc);
     ctx->d_bad = al.arr<unsigned>(1);
     ctx->sc.st = al.arr<DevStep>(1);
@@ -1374,6 +1384,7 @@ ccmc_status ccmc_batch_create(ccmc_ctx **ctxs, int32_t n, void *cuda_stream, ccm
         lim.scan_grid = std::min(lim.scan_grid, ctxs[r]->sc.sh.scan_grid);
         lim.work_grid = std::min(lim.work_grid, ctxs[r]->sc.sh.work_grid);
         lim.sort_grid = std::min(lim.sort_grid, ctxs[r]->sc.sh.sort_grid);
+        lim.nranks = std::max(lim.nranks, ctxs[r]->sc.sh.nranks);
     }
     lim.digit_bits = MAX_DIGIT_BITS;
     b->lim = lim;

@@ -129,7 +129,9 @@ __host__ __device__ __forceinline__ void mulhilo64(u64 x, u64 m, u64 &hi, u64 &l
 
 __host__ __device__ __forceinline__ R4 philox(u64 c0, u64 c1, u64 c2, u64 c3, u64 k0, u64 k1)
 {
-#pragma unroll
+    // two rounds per loop iteration: the sampler inlines several draws, and
+    // fully unrolled rounds made its loop overflow the instruction cache
+#pragma unroll 2
     for (int r = 0; r < 10; r++) {
         const u64 m0 = 0xD2E7470EE14C6C93ULL, m1 = 0xCA5A826395121157ULL;
         u64 hi0, lo0, hi1, lo1;

@@ -247,8 +247,7 @@ __device__ __forceinline__ bool round_value(double x, u64 r, const RunParams &p,
 // smallest i in [1, n-1] with prefix[i] > x (excitor owning position x);
 // the bucket of x brackets the answer between the owners of its first
 // position and of the next bucket's first position
-template <int K>
-__device__ __forceinline__ i64 pick_index(const PickEntry<K> *pk, const int *bucket, int shift, i64 nbuckets, i64 n,
+__device__ __forceinline__ i64 pick_index(const PickEntry *pk, const int *bucket, int shift, i64 nbuckets, i64 n,
                                           u64 x)
 {
     i64 b = (i64)(x >> shift);
@@ -260,6 +259,31 @@ __device__ __forceinline__ i64 pick_index(const PickEntry<K> *pk, const int *buc
         else lo = mid + 1;
     }
     return lo;
+}
+
+// Simulated distribution (Sec. III): the excitor of processor q holding
+// position x in [0, N_q) of that processor's entries in list order -- the
+// chunk whose processor-q prefix brackets x, then a walk over the chunk;
+// -1 only if the tables were inconsistent
+__device__ __forceinline__ i64 local_pick(const WorkArrays &wa, const PickEntry *pk, i64 n, int lcs, i64 nlc, u64 q,
+                                          u64 x)
+{
+    const i64 *row = wa.lcp + (i64)q * nlc;
+    i64 lo = 0, hi = nlc - 1;   // last chunk c with row[c] <= x
+    while (lo < hi) {
+        const i64 mid = (lo + hi + 1) >> 1;
+        if ((u64)__ldg(&row[mid]) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    u64 acc = (u64)__ldg(&row[lo]);
+    const i64 b = lo << lcs, e = b + (1LL << lcs) < n ? b + (1LL << lcs) : n;
+    for (i64 i = b > 1 ? b : 1; i < e; i++) {
+        if (__ldg(&wa.owner[i]) != q) continue;
+        const i64 v = __ldg(&pk[i].pop);
+        acc += (u64)(v < 0 ? -v : v);
+        if (acc > x) return i;
+    }
+    return -1;
 }
 
 // smallest i in [lo, hi] with end[i] > t (the answer is known to lie there)
@@ -643,7 +667,10 @@ __device__ __forceinline__ void d_scan_top(const ListView &L, DevStep *st, const
         double nex_d = (double)tw / FIX_ONE;
         double n0_d = (double)an0 / FIX_ONE;
         int smax = lmax + 2;
-        for (int s = 0; s < 8; s++) st->mag[s] = 0.0;
+        for (int s = 0; s < 8; s++) {
+            st->mag[s] = 0.0;
+            st->mden[s] = 0.0;
+        }
         for (int s = 0; s <= smax && n_sel > 0; s++) {
             double pr;
             if (p.fnc) {
@@ -664,13 +691,16 @@ __device__ __forceinline__ void d_scan_top(const ListView &L, DevStep *st, const
             den = den * pr;
             den = den * fact;
             st->mag[s] = num / den;
-            // N_p simulated processors: a composite cluster is co-located
-            // with probability N_p^-(s-1), so its amplitude carries N_p^(s-1)
-            if (s >= 2 && p.nranks > 1) {
-                double f = 1.0;
-                for (int e = 1; e < s; e++) f = f * (double)p.nranks;
-                st->mag[s] = st->mag[s] * f;
-            }
+            st->mden[s] = den;
+        }
+        // simulated distribution: chunks of 2^lcs entries, as fine as the
+        // per-processor position table allows
+        if (p.nranks > 1) {
+            const i64 n = st->n_occ;
+            int c = 5;
+            while (c < 40 && (i64)p.nranks * ((n + (1LL << c) - 1) >> c) > wa.lcp_cap) c++;
+            st->lcs = c;
+            st->nlc = (n + (1LL << c) - 1) >> c;
         }
         // every cluster of size s has |A| = mag[s]: its attempt count and
         // the magnitude of one attempt's coefficient, once per step
@@ -711,11 +741,11 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
         i64 w = (ok && i > 0) ? av : 0;
         double amp = (double)v / FIX_ONE;
         i64 na = (ok && p.fnc) ? attempts_of(fabs(amp), p) : 0;
-        i64 tw, ta;
+        i64 tw, ta = 0, ia = 0;
         i64 iw = block_incl_scan(w, sm, tw);
-        i64 ia = block_incl_scan(na, sm, ta);
+        if (p.fnc) ia = block_incl_scan(na, sm, ta);   // attempt prefix: full non-composite visits only
         if (ok) {
-            PickEntry<K> pe;
+            PickEntry pe;
             pe.prefix = cw + iw;
             pe.pop = v;
             pe.href = 0.0;
@@ -738,8 +768,6 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
             const double td = p.tau * ((i == 0 ? 0.0 : L.diag[i]) - S);
             pe.tdeath = td;
             const Det<K> d = load_det<K>(L.bits, L.cap, i);
-#pragma unroll
-            for (int q = 0; q < K; q++) pe.w[q] = d.w[q];
             i64 dv = 0;
             if (p.fnc) {
                 wa.att_end[i] = ca + ia;
@@ -757,7 +785,7 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
                 const int lev = level_of(s, d);
                 pe.href = (lev == 1 || lev == 2) ? h_ref<K, R>(s, d) : 0.0;
             }
-            ((PickEntry<K> *)wa.picks)[i] = pe;
+            wa.picks[i] = pe;
             wa.death[i] = dv;
         }
         cw += tw;
@@ -771,16 +799,68 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
     if (err) atomicOr(&st->err, err);   // every thread reports its own bits
 }
 
+// Simulated distribution (Sec. III): the owner of every excitor at this
+// iteration (Eq. ccmc_dist) and, per chunk of 2^lcs list entries, the |pop|
+// each processor holds in it; one warp per chunk, which clears its column of
+// the table first (integer sums: the table does not depend on the order)
+template <int K>
+__device__ __forceinline__ void d_local_table(const ListView &L, const DevStep *st, const RunParams &p, const WorkArrays &wa)
+{
+    if (p.nranks <= 1) return;
+    const i64 n = st->n_occ, nlc = st->nlc;
+    const int lcs = st->lcs, lane = threadIdx.x & 31;
+    const u64 it = st->iter;
+    const i64 nw = (i64)gridDim.x * (blockDim.x / 32);
+    for (i64 c = (i64)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); c < nlc; c += nw) {
+        for (i64 q = lane; q < p.nranks; q += 32) wa.lcp[q * nlc + c] = 0;
+        __syncwarp();
+        const i64 b = c << lcs, e = b + (1LL << lcs) < n ? b + (1LL << lcs) : n;
+        for (i64 i = b + lane; i < e; i += 32) {
+            if (i == 0) continue;   // the reference is not an excitor
+            const Det<K> d = load_det<K>(L.bits, L.cap, i);
+            const u64 q = words_owner(d.w, K, it, p.nu_move, (u64)p.nranks);
+            wa.owner[i] = (unsigned short)q;
+            const i64 v = L.pop[i];
+            atomicAdd((unsigned long long *)&wa.lcp[(i64)q * nlc + c], (unsigned long long)(v < 0 ? -v : v));
+        }
+        __syncwarp();
+    }
+}
+
+// each processor's row of the table turned into exclusive prefixes over the
+// chunks; its total is N_q
+__device__ __forceinline__ void d_local_scan(const DevStep *st, const RunParams &p, const WorkArrays &wa)
+{
+    __shared__ i64 sm[32];
+    if (p.nranks <= 1) return;
+    const i64 nlc = st->nlc;
+    for (i64 q = blockIdx.x; q < p.nranks; q += gridDim.x) {
+        i64 *row = wa.lcp + q * nlc;
+        i64 carry = 0;
+        for (i64 base = 0; base < nlc; base += blockDim.x) {
+            const i64 c = base + threadIdx.x;
+            const i64 v = c < nlc ? row[c] : 0;
+            i64 tot;
+            const i64 incl = block_incl_scan(v, sm, tot);
+            if (c < nlc) row[c] = carry + incl - v;
+            carry += tot;
+        }
+        if (threadIdx.x == 0) wa.nq[q] = carry;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // a2-a5: cluster sampling (Sec. II; composites only with FNC, Sec. IV.B)
 // ---------------------------------------------------------------------------
 
-template <int K, typename R>
+// DIST: the simulated distribution's restricted composite draw is compiled
+// in (a separate instantiation keeps it out of the plain sampler's loop)
+template <int K, typename R, bool DIST>
 __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, DevStep *st, const RunParams &p, const WorkArrays &wa,
                                                          const SpawnBuf &sp, const ClusterBuf &cl, int enum_base,
                                                          int vb, int vg)
 {
-    __shared__ double smag[8], scmag[8];
+    __shared__ double smag[8], scmag[8], smden[8];
     __shared__ i64 snatt[8];
     __shared__ u64 smf[64];
     __shared__ i64 sm[32];
@@ -792,6 +872,7 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
         smag[threadIdx.x] = st->mag[threadIdx.x];
         scmag[threadIdx.x] = st->cmag[threadIdx.x];
         snatt[threadIdx.x] = st->natt_s[threadIdx.x];
+        smden[threadIdx.x] = st->mden[threadIdx.x];
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -801,6 +882,8 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
     const i64 n_sel = st->n_sel, n = st->n_occ, nex = st->nex, n0 = st->n0;
     const int bshift = st->bucket_shift;
     const i64 nbk = st->nbuckets;
+    const int lcs = st->lcs;
+    const i64 nlc = st->nlc;
     const u64 it = st->iter;
     const double S = st->shift;
     Fix128 es = {0, 0};
@@ -810,7 +893,7 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
     i64 death_hf = 0;      // reference-cluster deaths, summed per block at the end
     i64 ndirect = 0;       // records added directly to listed determinants
     const DirectView dv = direct_view(L, wa, st);
-    const PickEntry<K> *pk = (const PickEntry<K> *)wa.picks;
+    const PickEntry *pk = wa.picks;
     // each warp runs its 32 samples of every block tile on its own: the
     // appends are staged per warp, so no block barrier is needed in the loop
     for (i64 g0 = (i64)vb * blockDim.x + 32 * wid; g0 < n_sel; g0 += (i64)vg * blockDim.x) {
@@ -844,10 +927,28 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
                 if (sz > 2) r1 = draw(p.seed, p.replica, it, TAG_SAMPLE, (u64)g, 1);
                 i64 idx[6];
                 int neg = 0;
-                // the picks are independent: issue all searches before using them
-                for (int e = 0; e < sz; e++) {
-                    u64 rr = e < 2 ? r0.v[2 + e] : r1.v[e - 2];
-                    idx[e] = pick_index<K>(pk, wa.bucket, bshift, nbk, n, below(rr, (u64)nex));
+                // simulated distribution: a composite's later excitors come
+                // from the first one's processor q (Sec. III)
+                const bool local = DIST && p.nranks > 1 && sz >= 2;
+                i64 nq = 0;
+                if (!local) {
+                    // the picks are independent: issue all searches before using them
+                    for (int e = 0; e < sz; e++) {
+                        u64 rr = e < 2 ? r0.v[2 + e] : r1.v[e - 2];
+                        idx[e] = pick_index(pk, wa.bucket, bshift, nbk, n, below(rr, (u64)nex));
+                    }
+                } else {
+                    idx[0] = pick_index(pk, wa.bucket, bshift, nbk, n, below(r0.v[2], (u64)nex));
+                    const u64 q = __ldg(&wa.owner[idx[0]]);
+                    nq = __ldg(&wa.nq[q]);
+                    for (int e = 1; e < sz; e++) {
+                        u64 rr = e < 2 ? r0.v[2 + e] : r1.v[e - 2];
+                        idx[e] = local_pick(wa, pk, n, lcs, nlc, q, below(rr, (u64)nq));
+                        if (idx[e] < 0) {
+                            valid = false;
+                            err |= ERRB_NUMERIC;
+                        }
+                    }
                 }
                 for (int e = 1; e < sz; e++)
                     for (int f = 0; f < e; f++)
@@ -857,30 +958,28 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
                     // applying it to HF (the closed form of the same product)
                     const i64 id = idx[0];
                     if (__ldg(&pk[id].pop) < 0) neg ^= 1;
-#pragma unroll
-                    for (int q = 0; q < K; q++) dj.w[q] = __ldg(&pk[id].w[q]);
+                    dj = load_det<K>(L.bits, L.cap, id);
                     par = excitor_sign(s, dj) < 0 ? 1 : 0;
                 } else {
-                    u64 own0 = 0;
                     for (int e = 0; e < sz && valid; e++) {
                         const i64 id = idx[e];
                         if (__ldg(&pk[id].pop) < 0) neg ^= 1;
-                        Det<K> de;
-#pragma unroll
-                        for (int q = 0; q < K; q++) de.w[q] = __ldg(&pk[id].w[q]);
-                        if (p.nranks > 1) {
-                            // simulated distribution: a composite cluster is
-                            // formed only from excitors on one processor
-                            const u64 ow = words_owner(de.w, K, it, p.nu_move, (u64)p.nranks);
-                            if (e == 0) own0 = ow;
-                            else if (ow != own0) valid = false;
-                        }
-                        if (valid && !apply_excitor(s, de, dj, par)) valid = false;   // shared orbital
+                        const Det<K> de = load_det<K>(L.bits, L.cap, id);
+                        if (!apply_excitor(s, de, dj, par)) valid = false;   // shared orbital
                     }
                 }
                 if (valid) {
                     if (n0 < 0 && ((sz - 1) & 1)) neg ^= 1;
-                    amp = neg ? -smag[sz] : smag[sz];
+                    double a = smag[sz];
+                    if (local) {
+                        // |A| = N_ex (N_q N_p)^(s-1) / (|t_HF|^(s-1) n_sel p(s) s!):
+                        // selection within q times co-location N_p^-(s-1)
+                        const double f = ((double)nq / FIX_ONE) * (double)p.nranks;
+                        double num = (double)nex / FIX_ONE;
+                        for (int e = 1; e < sz; e++) num = num * f;
+                        a = num / smden[sz];
+                    }
+                    amp = neg ? -a : a;
                     idx0 = idx[0];
                 }
             }
@@ -912,14 +1011,18 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
                         rec = true;
                     }
                 }
-                natt = snatt[sz];   // = attempts_of(|amp|): |amp| = mag[sz] for every cluster of size sz
+                // = attempts_of(|amp|): |amp| = mag[sz] for every cluster of
+                // size sz, unless its processor's population sets it
+                const bool local_amp = DIST && p.nranks > 1 && sz >= 2;
+                natt = local_amp ? attempts_of(fabs(amp), p) : snatt[sz];
                 valid_cl = true;
                 if (p.buffered) {
                     catt = coef;    // the original sampler's one attempt
                     cl_att += 1;
                 } else if (p.multispawn) {
                     // coef / natt: the same division, done once per size
-                    catt = natt > 1 ? (coef < 0.0 ? -scmag[sz] : scmag[sz]) : coef;
+                    if (local_amp) catt = natt > 1 ? coef / (double)natt : coef;
+                    else catt = natt > 1 ? (coef < 0.0 ? -scmag[sz] : scmag[sz]) : coef;
                     if (natt > p.work_cap) {   // runaway: the attempts kernel will not run them
                         err |= ERRB_RUNAWAY;
                         natt = p.work_cap + 1;
@@ -1297,42 +1400,46 @@ __device__ __forceinline__ void d_merge_match(const ListView &L, DevStep *st, co
     }
 }
 
-__device__ __forceinline__ void d_merge_list(const ListView &L, DevStep *st, const RunParams &p, const WorkArrays &wa)
-{
-    __shared__ i64 sm[32];
-    const i64 n = st->n_occ;
-    const u64 it = st->iter;
-    const bool direct = st->nkb > 0;
-    i64 hits = 0;   // entries that received directly added spawns: distinct keys of the step
-    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
-        i64 v = L.pop[i] + wa.death[i] + wa.acc[i];
-        if (i > 0) v = threshold(p, it, L.key[i], v);
-        wa.newpop[i] = v;
-        // two counts in one word (each below 2^31): the entry's keep flag and
-        // the kept new keys that go before it; one prefix gives both
-        wa.keep_l[i] = ((i == 0 || v != 0) ? 1 : 0) | ((i64)wa.before[i] << 32);
-        if (direct) hits += wa.hit[i];
-    }
-    if (direct) {
-        hits = block_sum(hits, sm);
-        if (threadIdx.x == 0 && hits) atomicAdd((unsigned long long *)&st->n_hit, (unsigned long long)hits);
-    }
-}
-
-// counts of kept list entries (blocks [0, G)) and kept new keys ([G, 2G))
-__device__ __forceinline__ void d_keep_count(const DevStep *st, const WorkArrays &wa, int G)
+// New populations of the list entries (old + death + matched spawns, then the
+// occupation threshold) with their keep flags packed with the kept new keys
+// inserted before them (blocks [0, G), contiguous chunks), and the keep counts
+// of the new keys (blocks [G, 2G)); each block's sum goes to the partials.
+__device__ __forceinline__ void d_merge_count(const ListView &L, DevStep *st, const RunParams &p, const WorkArrays &wa,
+                                              int G)
 {
     __shared__ i64 sm[32];
     const bool second = blockIdx.x >= G;
     const i64 n = second ? st->n_keys : st->n_occ;
-    const i64 *f = second ? wa.keep_s : wa.keep_l;
-    i64 c = (n + G - 1) / G;
-    i64 b = second ? blockIdx.x - G : blockIdx.x;
-    i64 lo = b * c < n ? b * c : n, hi = lo + c < n ? lo + c : n;
-    i64 s = 0;
-    for (i64 i = lo + threadIdx.x; i < hi; i += blockDim.x) s += f[i];
-    s = block_sum(s, sm);
-    if (threadIdx.x == 0) wa.part[4 * blockIdx.x] = s;
+    const i64 c = (n + G - 1) / G;
+    const i64 b = second ? blockIdx.x - G : blockIdx.x;
+    const i64 lo = b * c < n ? b * c : n, hi = lo + c < n ? lo + c : n;
+    i64 sum = 0;
+    if (second) {
+        for (i64 i = lo + threadIdx.x; i < hi; i += blockDim.x) sum += wa.keep_s[i];
+    } else {
+        const u64 it = st->iter;
+        const bool direct = st->nkb > 0;
+        i64 hits = 0;   // entries that received directly added spawns: distinct keys of the step
+        for (i64 i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            i64 v = L.pop[i] + wa.death[i] + wa.acc[i];
+            // the key is read only for the few entries the threshold decides
+            const i64 av = v < 0 ? -v : v;
+            if (i > 0 && av > 0 && av < (i64)FIX_ONE) v = threshold(p, it, L.key[i], v);
+            wa.newpop[i] = v;
+            // two counts in one word (each below 2^31): the entry's keep flag
+            // and the kept new keys that go before it; one prefix gives both
+            const i64 w = ((i == 0 || v != 0) ? 1 : 0) | ((i64)wa.before[i] << 32);
+            wa.keep_l[i] = w;
+            sum += w;
+            if (direct) hits += wa.hit[i];
+        }
+        if (direct) {
+            hits = block_sum(hits, sm);
+            if (threadIdx.x == 0 && hits) atomicAdd((unsigned long long *)&st->n_hit, (unsigned long long)hits);
+        }
+    }
+    sum = block_sum(sum, sm);
+    if (threadIdx.x == 0) wa.part[4 * blockIdx.x] = sum;
 }
 
 // exclusive prefixes of the keep flags in place
@@ -1396,6 +1503,79 @@ __device__ __forceinline__ void d_scatter_list(const SysDev &s, const ListView &
         O.pop[out] = v;
         O.diag[out] = L.diag[i];
         asum += v < 0 ? -v : v;
+    }
+    asum = block_sum(asum, sm);
+    if (threadIdx.x == 0) {
+        if (asum) atomicAdd((unsigned long long *)&st->ntot_after, (unsigned long long)asum);
+    }
+    if (err) atomicOr(&st->err, err);   // every thread reports its own bits
+}
+
+// The keep prefixes and the list's scatter in one pass.  Blocks [G, 2G):
+// exclusive prefix of the new keys' keep flags in place.  Blocks [0, G): the
+// exclusive prefix e of the packed list words (kept entries | kept new keys
+// before the entry << 32) over the block's chunk, four rows of the block in
+// flight at a time; each kept entry goes to e_lo + e_hi + (new keys right
+// before it), and e is stored only where kept new keys are inserted (the
+// new-key scatter reads it there).
+template <int K>
+__device__ __forceinline__ void d_keep_scatter(const ListView &L, const ListView &O, DevStep *st, const WorkArrays &wa,
+                                               int G)
+{
+    __shared__ i64 sm[32];
+    const bool second = blockIdx.x >= G;
+    const i64 n = second ? st->n_keys : st->n_occ;
+    const i64 c = (n + G - 1) / G;
+    const i64 b = second ? blockIdx.x - G : blockIdx.x;
+    const i64 lo = b * c < n ? b * c : n, hi = lo + c < n ? lo + c : n;
+    i64 carry = wa.part[4 * blockIdx.x + 2];
+    if (second) {
+        for (i64 base = lo; base < hi; base += blockDim.x) {
+            const i64 i = base + threadIdx.x;
+            const i64 v = i < hi ? wa.keep_s[i] : 0;
+            i64 tot;
+            const i64 incl = block_incl_scan(v, sm, tot);
+            if (i < hi) wa.keep_s[i] = carry + incl - v;
+            carry += tot;
+        }
+        return;
+    }
+    constexpr int ROWS = 4;
+    i64 asum = 0;
+    unsigned err = 0;
+    for (i64 base = lo; base < hi; base += ROWS * (i64)blockDim.x) {
+        i64 w[ROWS], v[ROWS], e[ROWS];
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) {
+            const i64 i = base + r * (i64)blockDim.x + threadIdx.x;
+            w[r] = i < hi ? wa.keep_l[i] : 0;
+            v[r] = i < hi ? wa.newpop[i] : 0;
+        }
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) {
+            i64 tot;
+            const i64 incl = block_incl_scan(w[r], sm, tot);
+            e[r] = carry + incl - w[r];
+            carry += tot;
+        }
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) {
+            const i64 i = base + r * (i64)blockDim.x + threadIdx.x;
+            if (i >= hi) continue;
+            const i64 nb = w[r] >> 32;   // kept new keys inserted right before entry i
+            if (nb) wa.keep_l[i] = e[r];
+            if (!(i == 0 || v[r] != 0)) continue;
+            const i64 out = (e[r] & 0xFFFFFFFFLL) + (e[r] >> 32) + nb;
+            if (out >= O.cap) {
+                err |= ERRB_LIST_OVERFLOW;
+                continue;
+            }
+            store_det<K>(O.bits, O.cap, out, load_det<K>(L.bits, L.cap, i));
+            O.key[out] = L.key[i];
+            O.pop[out] = v[r];
+            O.diag[out] = L.diag[i];
+            asum += v[r] < 0 ? -v[r] : v[r];
+        }
     }
     asum = block_sum(asum, sm);
     if (threadIdx.x == 0) {
@@ -1516,8 +1696,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_seg_count(const StepArgs *__re
 __global__ void __launch_bounds__(1024) k_part_scan(const StepArgs *__restrict__ A, int grid);
 __global__ void __launch_bounds__(SCAN_THREADS) k_seg_write(const StepArgs *__restrict__ A, int src);
 __global__ void __launch_bounds__(WORK_THREADS) k_merge_match(const StepArgs *__restrict__ A, int src);
-__global__ void __launch_bounds__(WORK_THREADS) k_merge_list(const StepArgs *__restrict__ A);
-__global__ void __launch_bounds__(SCAN_THREADS) k_keep_count(const StepArgs *__restrict__ A, int G);
+__global__ void __launch_bounds__(SCAN_THREADS) k_merge_count(const StepArgs *__restrict__ A, int G);
+__global__ void __launch_bounds__(SCAN_THREADS) k_local_scan(const StepArgs *__restrict__ A);
 __global__ void __launch_bounds__(1024) k_keep_top(const StepArgs *__restrict__ A, int G);
 __global__ void __launch_bounds__(SCAN_THREADS) k_keep_final(const StepArgs *__restrict__ A, int G);
 __global__ void __launch_bounds__(1024) k_finalize(const StepArgs *__restrict__ A, int slots);
@@ -1529,16 +1709,16 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(const StepArgs *__r
     d_scan_final<K, R>(a.s, a.list[cur_], a.st, a.p, a.wa);
 }
 
-template <int K, typename R>
+template <int K, typename R, bool DIST>
 __global__ void __launch_bounds__(WORK_THREADS, SAMPLE_BLOCKS_PER_SM) k_sample(const StepArgs *__restrict__ A, int enum_base)
 {
     REPLICA_SMEM;
-    d_sample<K, R>(a.s, a.list[cur_], a.st, a.p, a.wa, a.sp, a.cl, enum_base, blockIdx.x, gridDim.x);
+    d_sample<K, R, DIST>(a.s, a.list[cur_], a.st, a.p, a.wa, a.sp, a.cl, enum_base, blockIdx.x, gridDim.x);
 }
 
 // Persistent batch sampler: each block takes the next virtual block of the
 // plan, finds its replica and runs that share of the replica's samples.
-template <int K, typename R>
+template <int K, typename R, bool DIST>
 __global__ void __launch_bounds__(WORK_THREADS, SAMPLE_BLOCKS_PER_SM) k_sample_flat(const StepArgs *__restrict__ A, int nrep, FlatPlan fp,
                                                                  int enum_base)
 {
@@ -1576,7 +1756,7 @@ __global__ void __launch_bounds__(WORK_THREADS, SAMPLE_BLOCKS_PER_SM) k_sample_f
         }
         const StepArgs &a = a_sm;
         const int v0 = fp.vstart[r];
-        d_sample<K, R>(a.s, a.list[a.st->cur], a.st, a.p, a.wa, a.sp, a.cl, enum_base, v - v0,
+        d_sample<K, R, DIST>(a.s, a.list[a.st->cur], a.st, a.p, a.wa, a.sp, a.cl, enum_base, v - v0,
                        fp.vstart[r + 1] - v0);
     }
 }
@@ -1586,6 +1766,20 @@ __global__ void __launch_bounds__(WORK_THREADS, 4) k_attempts(const StepArgs *__
 {
     REPLICA_SMEM;
     d_attempts<K, R>(a.s, a.list[cur_], a.st, a.p, a.wa, a.sp, a.cl);
+}
+
+template <int K>
+__global__ void __launch_bounds__(WORK_THREADS) k_local_table(const StepArgs *__restrict__ A)
+{
+    REPLICA;
+    d_local_table<K>(a.list[cur_], a.st, a.p, a.wa);
+}
+
+template <int K>
+__global__ void __launch_bounds__(SCAN_THREADS) k_keep_scatter(const StepArgs *__restrict__ A, int G)
+{
+    REPLICA;
+    d_keep_scatter<K>(a.list[cur_], a.list[cur_ ^ 1], a.st, a.wa, G);
 }
 
 template <int K>
@@ -1620,13 +1814,21 @@ cudaError_t launch_phases(const StepArgs *A, int nrep, const Shapes &sh, bool mu
     k_scan_top<<<gone, 1024, 0, sm>>>(A, sh.scan_grid);
     k_scan_final<K, R><<<gscan, SCAN_THREADS, 0, sm>>>(A);
     launches[0] += 3;
+    if (sh.nranks > 1) {
+        // simulated distribution: owners and per-processor position tables
+        k_local_table<K><<<gwork, WORK_THREADS, 0, sm>>>(A);
+        k_local_scan<<<dim3(sh.nranks < 1024 ? sh.nranks : 1024, nrep), SCAN_THREADS, 0, sm>>>(A);
+        launches[0] += 2;
+    }
     mark(1);
     if (plan) {
         k_sample_plan<<<1, 1024, 0, sm>>>(A, nrep, *plan, sh.scan_grid);
-        k_sample_flat<K, R><<<plan->grid, WORK_THREADS, 0, sm>>>(A, nrep, *plan, sh.scan_grid);
+        if (sh.nranks > 1) k_sample_flat<K, R, true><<<plan->grid, WORK_THREADS, 0, sm>>>(A, nrep, *plan, sh.scan_grid);
+        else k_sample_flat<K, R, false><<<plan->grid, WORK_THREADS, 0, sm>>>(A, nrep, *plan, sh.scan_grid);
         launches[1] += 2;
     } else {
-        k_sample<K, R><<<gwork, WORK_THREADS, 0, sm>>>(A, sh.scan_grid);
+        if (sh.nranks > 1) k_sample<K, R, true><<<gwork, WORK_THREADS, 0, sm>>>(A, sh.scan_grid);
+        else k_sample<K, R, false><<<gwork, WORK_THREADS, 0, sm>>>(A, sh.scan_grid);
         launches[1] += 1;
     }
     mark(2);
@@ -1651,13 +1853,11 @@ cudaError_t launch_phases(const StepArgs *A, int nrep, const Shapes &sh, bool mu
     launches[4] += 3;
     mark(5);
     k_merge_match<<<gwork, WORK_THREADS, 0, sm>>>(A, src);
-    k_merge_list<<<gwork, WORK_THREADS, 0, sm>>>(A);
-    k_keep_count<<<dim3(2 * sh.scan_grid, nrep), SCAN_THREADS, 0, sm>>>(A, sh.scan_grid);
+    k_merge_count<<<dim3(2 * sh.scan_grid, nrep), SCAN_THREADS, 0, sm>>>(A, sh.scan_grid);
     k_keep_top<<<gone, 1024, 0, sm>>>(A, sh.scan_grid);
-    k_keep_final<<<dim3(2 * sh.scan_grid, nrep), SCAN_THREADS, 0, sm>>>(A, sh.scan_grid);
-    k_scatter_list<K><<<gwork, WORK_THREADS, 0, sm>>>(A, src);
+    k_keep_scatter<K><<<dim3(2 * sh.scan_grid, nrep), SCAN_THREADS, 0, sm>>>(A, sh.scan_grid);
     k_scatter_new<K, R><<<gwork, WORK_THREADS, 0, sm>>>(A, src);
-    launches[5] += 7;
+    launches[5] += 5;
     mark(6);
     k_finalize<<<gone, 1024, 0, sm>>>(A, plan ? sh.scan_grid + plan->wmax : sh.enum_slots);
     launches[6] += 1;

@@ -34,7 +34,7 @@ struct RunParams {
     int a_thresh_one;     // A_thresh == 1: floor(|A|) without a division
     int direct;           // spawns onto listed determinants are added to them directly (not sorted)
     int buffered;         // original sampler: each valid cluster's one attempt runs in the attempts kernel
-    int nranks;           // simulated processors (Sec. III): composite clusters only from co-located excitors
+    int nranks;           // simulated processors (Sec. III): composite clusters from one processor's excitors
     int nu_move;          // owners move every 2^nu_move iterations (>= 64: never)
     i64 work_cap;         // samples, visit attempts or cluster attempts per step beyond which the step is abandoned
     RoundSpec spawn_rs;   // spawn rounding (with the cutoff)
@@ -89,6 +89,13 @@ struct DevStep {
     i64 n_direct;       // spawned records added directly to listed determinants
     i64 n_hit;          // listed determinants that received such records
     i64 prev_spawned;   // spawned records of the previous step (0 after a list upload)
+    // simulated distribution (Sec. III): the denominators of |A_s| (a
+    // composite's amplitude depends on its processor's population), and the
+    // chunks of the per-processor position table
+    double mden[8];
+    int lcs;            // chunks cover 2^lcs list entries
+    int pad2;
+    i64 nlc;            // chunks in use
 };
 
 // Spawn buffer pair for the radix sort (ping-pong).
@@ -107,25 +114,20 @@ struct ClusterBuf {
     i64 cap;
 };
 
-// The cluster sampler's view of one list entry, written by the scans each
-// step and gathered by a pick in one place (32-byte sectors, 64 bytes for up
-// to four words): selection prefix, population, death factor, <HF|H|D> and
-// the bit string.
-template <int K>
+// The cluster sampler's view of one list entry besides its bit string,
+// written by the scans each step and gathered by a pick as one 32-byte
+// sector: selection prefix, population, death factor and <HF|H|D>.
 struct __align__(32) PickEntry {
     i64 prefix;     // inclusive |pop| prefix over entries >= 1 (entry 0: 0)
     i64 pop;
     double tdeath;  // tau (Delta E_i - S): the death factor of this step
     double href;    // <HF|H|D_i> (levels 1-2; 0 otherwise; 0 with full non-composite sampling)
-    u64 w[K];
 };
-
-static_assert(sizeof(PickEntry<2>) == 64 && sizeof(PickEntry<4>) == 64 && sizeof(PickEntry<6>) == 96,
-              "pick table rows: 64 bytes up to four words, 96 above");
+static_assert(sizeof(PickEntry) == 32, "pick table rows are one 32-byte sector");
 
 // Per-step work arrays over the list and the merge.
 struct WorkArrays {
-    void *picks;      // PickEntry<K>[list capacity]
+    PickEntry *picks; // one row per list entry
     int *bucket;      // owner of the first position of each selection bucket
     int bucket_bits;  // log2 of the bucket capacity
     i64 *att_end;     // inclusive prefix of full non-composite attempts
@@ -145,6 +147,11 @@ struct WorkArrays {
     unsigned *hist;   // radix histograms, digit-major (2^bits x sort grid)
     unsigned *hist_tot;  // per-digit totals of the current pass
     Record *ring;     // per-step records
+    // simulated distribution (Sec. III), allocated only with N_p > 1
+    unsigned short *owner;  // processor of each list entry at this iteration
+    i64 *lcp;         // [q][chunk]: |pop| of processor q's entries before the chunk
+    i64 *nq;          // N_q: |pop| held by processor q
+    i64 lcp_cap;      // capacity of lcp
 };
 
 // Grid shapes chosen once per context.
@@ -155,6 +162,7 @@ struct Shapes {
     int digit_bits;   // radix digit width
     int key_bits;     // significant key bits
     int enum_slots;   // scan_grid + work_grid (E_num partials of the scans and the sampler)
+    int nranks;       // simulated processors (largest over the replicas; 1: none)
 };
 
 // Per-replica arguments of the step kernels (device-resident; a single

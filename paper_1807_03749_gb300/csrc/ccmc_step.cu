@@ -6,7 +6,7 @@
 //
 //  a1  k_scan_partial / k_scan_top           a7  k_sort_hist / scan / scatter
 //  a8  k_seg_count / k_part_scan / k_seg_write
-//  a9  k_merge_match / k_merge_list / k_keep_count / top / final
+//  a9  k_merge_match / k_merge_count / k_keep_top / k_keep_final
 //  a10 k_finalize      batch: k_sample_plan
 //  ccmc_reduce_records_noalloc (end of file): the sort and reduction as a
 //      standalone call on a static scratch array
@@ -116,16 +116,16 @@ __global__ void __launch_bounds__(WORK_THREADS) k_merge_match(const StepArgs *__
     d_merge_match(a.list[cur_], a.st, a.p, a.wa, a.sp.key[src ^ 1], a.sp.pop[src ^ 1]);
 }
 
-__global__ void __launch_bounds__(WORK_THREADS) k_merge_list(const StepArgs *__restrict__ A)
+__global__ void __launch_bounds__(SCAN_THREADS) k_merge_count(const StepArgs *__restrict__ A, int G)
 {
     REPLICA;
-    d_merge_list(a.list[cur_], a.st, a.p, a.wa);
+    d_merge_count(a.list[cur_], a.st, a.p, a.wa, G);
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_keep_count(const StepArgs *__restrict__ A, int G)
+__global__ void __launch_bounds__(SCAN_THREADS) k_local_scan(const StepArgs *__restrict__ A)
 {
     const StepArgs &a = A[blockIdx.y];
-    d_keep_count(a.st, a.wa, G);
+    d_local_scan(a.st, a.p, a.wa);
 }
 
 __global__ void __launch_bounds__(1024) k_keep_top(const StepArgs *__restrict__ A, int G)

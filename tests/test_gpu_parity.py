@@ -359,6 +359,24 @@ def test_distributed_sampling_bitexact(ccmc):
     assert not np.array_equal(ctx1.get_list()[2], ctx.get_list()[2])
 
 
+def test_distributed_sampling_original_and_many_ranks(ccmc):
+    """The restricted composite picks with the original sampler on a small
+    molecule (buffered single attempts, singles present), and with 30,000
+    processors, where the position table needs chunks of up to 128 entries
+    and most processors hold at most one excitor."""
+    h1, eri = molecule_integrals(norb=8, nocc=3, seed=5, scale=0.1)
+    wm = dict(kind="generic", nel=6, norb=8, nso=16, lmax=3, h1=h1, eri=eri, tau=0.01, target_pop=3000.0,
+              d0_init=400.0, shift_a=10, zeta=0.05, spawn_cutoff=2.0 ** -7, a_thresh=1.0, seed=3, replica=0,
+              fnc=0, multispawn=0, n_ranks=5, nu_move=0)
+    so, sim, ctx = _pair(ccmc, wm)
+    _run_lockstep(sim, ctx, 80, check_spawned_every=20)
+    w = workload("ueg14_m66_ccsdt_rs5", target_pop=2e5, d0_init=2e4, tau=0.01, multispawn=True, n_ranks=30000,
+                 nu_move=3)
+    so, sim, ctx = _pair(ccmc, w)
+    _run_lockstep(sim, ctx, 80, check_spawned_every=20)
+    assert ctx.get_list()[0].shape[0] > 8000   # 30,000 x ceil(n / 64) > 2^22: 128-entry chunks
+
+
 def test_colocation_matches_oracle(ccmc):
     """Pair co-location sums of Fig. excitdistrib on the 3,813 excitors of the
     14-electron, 186 spin-orbital CCSD space: GPU and oracle agree exactly."""

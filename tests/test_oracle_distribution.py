@@ -7,10 +7,14 @@ over processors (Sec. III, Eq. ccmc_dist; Fig. excitdistrib; Fig. bias).
   reduction of Eq. ccmc_dist to Eq. fciqmc_dist), is constant over aligned
   runs of 2^nu_move iterations, and is uniform over the processors;
 * the pair co-location sums agree with a direct count, have the unbiased
-  mean 1/N_p and a spread that scales as sqrt((N_p - 1) / N_p^2 * 2^nu / T);
+  mean 1/N_p and the spread of a binomial law over the iterations whose
+  terms are correlated by the moves: sqrt((N_p - 1) / N_p^2 * F / T), F the
+  phased-moves factor (about 2^(nu+1)/3, against the 2^nu of moves aligned
+  across excitors);
 * the restricted sampler reduces to the plain one for N_p = 1 and, averaged
   over iterations (owners), its one-step mean equals the exact propagator
-  action (Sec. II, Eq. CCMC): the N_p^(s-1) amplitude factor is right.
+  action (Sec. II, Eq. CCMC): drawing the later excitors of a composite from
+  the first one's processor with the weight (N_q N_p / N_ex)^(s-1) is right.
 """
 import numpy as np
 import pytest
@@ -98,10 +102,32 @@ def test_colocation_sums_match_direct_count():
         assert int(s1[k]) == int(c.sum()) and int(s2[k]) == int((c.astype(np.int64) ** 2).sum())
 
 
-@pytest.mark.parametrize("np_,nu", [(8, 0), (8, 3), (32, 2)])
+def _phased_moves_factor(L: int, T: int) -> float:
+    """T x the variance of a pair's co-location average over T iterations,
+    in units of p(1 - p), p = 1/N_p.  The owner of each excitor changes every
+    L = 2^nu iterations at a phase set by its own hash (Eq. ccmc_dist), so
+    the co-location of two excitors is unchanged over d iterations only when
+    neither has moved: with independent uniform phases that has probability
+    (1 - d/L)^2, and once either moves the new co-location is independent of
+    the old.  Hence Var = p(1-p)/T^2 [T + 2 sum_{d=1}^{L-1} (T - d)(1 - d/L)^2],
+    which tends to (2L^2 + 1)/(3L) for T >> L (the binomial argument with
+    moves aligned across excitors would give L)."""
+    return (T + 2.0 * sum((T - d) * (1.0 - d / L) ** 2 for d in range(1, min(L, T)))) / T
+
+
+def test_phased_moves_factor_limits():
+    assert _phased_moves_factor(1, 100) == 1.0
+    for L in (2, 16, 64):
+        assert abs(_phased_moves_factor(L, 10 ** 7) - (2 * L * L + 1) / (3 * L)) < 1e-3 * L
+
+
+@pytest.mark.parametrize("np_,nu", [(8, 0), (8, 3), (32, 2), (5, 4)])
 def test_colocation_mean_and_spread_scaling(np_, nu):
     """Fig. excitdistrib: the mean co-location probability is unbiased (1/N_p)
-    and its spread over pairs follows the binomial law of T / 2^nu moves."""
+    and its spread over pairs follows the binomial law of p = 1/N_p over the
+    iterations, with the moves every 2^nu iterations correlating them (the
+    phased-moves factor above; an aligned-moves or an uncorrelated law would
+    be off by 22 % or more for nu >= 3)."""
     dets = _ueg_excitors(14, 38, 2)[:200]
     T = 512
     s1, s2 = oracle.colocation(dets, np_, nu, [T])
@@ -109,8 +135,9 @@ def test_colocation_mean_and_spread_scaling(np_, nu):
     mean = float(s1[0]) / (P * T)
     var = float(s2[0]) / (P * T * T) - mean * mean
     assert abs(mean * np_ - 1.0) < 0.05
-    expect = np.sqrt((np_ - 1) / np_ ** 2 * (2 ** nu) / T)
-    assert 0.6 < np.sqrt(var) / expect < 1.6
+    p = 1.0 / np_
+    expect = np.sqrt(p * (1 - p) * _phased_moves_factor(2 ** nu, T) / T)
+    assert abs(np.sqrt(var) / expect - 1.0) < 0.03
 
 
 def test_one_rank_is_the_plain_step():
@@ -124,8 +151,10 @@ def test_one_rank_is_the_plain_step():
 def test_distributed_step_mean_equals_exact_action():
     """With 3 simulated processors moving every iteration, the mean of one
     step over many iterations (owner configurations) and Philox keys equals
-    the exact action of the propagator: composite clusters are dropped unless
-    co-located and the survivors carry N_p^(s-1)."""
+    the exact action of the propagator: a composite cluster's later excitors
+    come from the first one's processor q only, and its amplitude carries
+    (N_q N_p / N_ex)^(s-1) (selection within q, co-location probability
+    N_p^-(s-1) averaged over owners)."""
     tau, shift = 0.01, 0.3
     h1, eri = tiny_molecule(norb=5, nocc=2, seed=11, scale=0.3)
     ham = brute.GenericBrute(4, h1, eri)
