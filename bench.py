@@ -145,7 +145,7 @@ def algorithmic_bytes(phase: str, recs: list, nw: int, lmax: int = 2, fnc: bool 
     (bits, attempt coefficient, sample index, attempt prefix).
       scan:     8 B read + 8 B written per entry
       sample:   s_mean * B_e gathered per sample, plus what the sampler writes:
-                16 B per record (original sampler) or one buffered cluster
+                16 B per record (inline attempts) or one buffered cluster
       attempts: each owner read once (list entries of the full
                 non-composite sweep, buffered clusters), 16 B per record
       sort:     one read and one write of each record entering it (16 + 16 B);
@@ -163,9 +163,11 @@ def algorithmic_bytes(phase: str, recs: list, nw: int, lmax: int = 2, fnc: bool 
         if phase == "scan":
             b = n * 16
         elif phase == "sample":
-            b = r["n_sel"] * sbar * be + (ncl * bc if multispawn else sp * 16)
+            # buffered clusters (multi-spawn, or the original sampler on a
+            # generic Hamiltonian): their records are the attempt kernel's
+            b = r["n_sel"] * sbar * be + (ncl * bc if ncl else sp * 16)
         elif phase == "attempts":
-            b = r["n_visit"] * be + ncl * bc + sp * 16
+            b = r["n_visit"] * be + ncl * bc + (sp * 16 if (ncl or r["n_visit"]) else 0)
         elif phase == "sort":
             b = (sp - r.get("n_direct", 0)) * 32
         elif phase == "reduce":
@@ -197,7 +199,7 @@ def read_profile(workload: str) -> dict:
     return out
 
 
-PHASE_OF_KERNEL = [("k_scan", "scan"), ("k_sample", "sample"), ("k_attempts", "attempts"), ("k_sort", "sort"),
+PHASE_OF_KERNEL = [("k_scan", "scan"), ("k_local", "scan"), ("k_sample", "sample"), ("k_attempts", "attempts"), ("k_sort", "sort"),
                    ("k_seg", "reduce"), ("k_part_scan", "reduce"), ("k_merge", "merge"), ("k_keep", "merge"),
                    ("k_scatter", "merge"), ("k_finalize", "finalize")]
 UNIT_OF_PHASE = {"scan": "entry", "sample": "sample", "attempts": "attempt", "sort": "record", "reduce": "record",

@@ -734,10 +734,17 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
     const double S = st->shift;
     Fix128 es = {0, 0};
     unsigned err = 0;
+    const bool kb = st->nkb > 0;
     for (i64 base = lo; base < hi; base += blockDim.x) {
         i64 i = base + threadIdx.x;
         bool ok = i < hi;
+        // every read of the entry is issued before the block scans, so that
+        // one memory latency per tile is exposed instead of two
         i64 v = ok ? L.pop[i] : 0, av = v < 0 ? -v : v;
+        const u64 key_i = ok && kb ? L.key[i] : 0, key_p = ok && kb && i > 0 ? L.key[i - 1] : 0;
+        const double diag_i = ok && i > 0 ? L.diag[i] : 0.0;
+        Det<K> d;
+        if (ok) d = load_det<K>(L.bits, L.cap, i);
         i64 w = (ok && i > 0) ? av : 0;
         double amp = (double)v / FIX_ONE;
         i64 na = (ok && p.fnc) ? attempts_of(fabs(amp), p) : 0;
@@ -758,16 +765,15 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
             }
             wa.acc[i] = 0;
             wa.before[i] = 0;
-            if (st->nkb > 0) {
+            if (kb) {
                 // buckets whose first key falls in (key[i-1], key[i]] start at entry i
                 const int ks = st->kshift;
-                const u64 b0 = i == 0 ? 0 : (L.key[i - 1] >> ks) + 1, b1 = L.key[i] >> ks;
+                const u64 b0 = i == 0 ? 0 : (key_p >> ks) + 1, b1 = key_i >> ks;
                 for (u64 b = b0; b <= b1; b++) wa.kbucket[b] = (int)i;
                 wa.hit[i] = 0;
             }
-            const double td = p.tau * ((i == 0 ? 0.0 : L.diag[i]) - S);
+            const double td = p.tau * ((i == 0 ? 0.0 : diag_i) - S);
             pe.tdeath = td;
-            const Det<K> d = load_det<K>(L.bits, L.cap, i);
             i64 dv = 0;
             if (p.fnc) {
                 wa.att_end[i] = ca + ia;
@@ -1420,18 +1426,32 @@ __device__ __forceinline__ void d_merge_count(const ListView &L, DevStep *st, co
         const u64 it = st->iter;
         const bool direct = st->nkb > 0;
         i64 hits = 0;   // entries that received directly added spawns: distinct keys of the step
-        for (i64 i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-            i64 v = L.pop[i] + wa.death[i] + wa.acc[i];
-            // the key is read only for the few entries the threshold decides
-            const i64 av = v < 0 ? -v : v;
-            if (i > 0 && av > 0 && av < (i64)FIX_ONE) v = threshold(p, it, L.key[i], v);
-            wa.newpop[i] = v;
-            // two counts in one word (each below 2^31): the entry's keep flag
-            // and the kept new keys that go before it; one prefix gives both
-            const i64 w = ((i == 0 || v != 0) ? 1 : 0) | ((i64)wa.before[i] << 32);
-            wa.keep_l[i] = w;
-            sum += w;
-            if (direct) hits += wa.hit[i];
+        constexpr int ROWS = 4;   // rows of the block whose reads are in flight together
+        for (i64 base = lo; base < hi; base += ROWS * (i64)blockDim.x) {
+            i64 v[ROWS], nb[ROWS], h[ROWS];
+#pragma unroll
+            for (int r = 0; r < ROWS; r++) {
+                const i64 i = base + r * (i64)blockDim.x + threadIdx.x;
+                v[r] = i < hi ? L.pop[i] + wa.death[i] + wa.acc[i] : 0;
+                nb[r] = i < hi ? wa.before[i] : 0;
+                h[r] = i < hi && direct ? wa.hit[i] : 0;
+            }
+#pragma unroll
+            for (int r = 0; r < ROWS; r++) {
+                const i64 i = base + r * (i64)blockDim.x + threadIdx.x;
+                if (i >= hi) continue;
+                // the key is read only for the few entries the threshold decides
+                const i64 av = v[r] < 0 ? -v[r] : v[r];
+                if (i > 0 && av > 0 && av < (i64)FIX_ONE) v[r] = threshold(p, it, L.key[i], v[r]);
+                wa.newpop[i] = v[r];
+                // two counts in one word (each below 2^31): the entry's keep
+                // flag and the kept new keys that go before it; one prefix
+                // gives both
+                const i64 w = ((i == 0 || v[r] != 0) ? 1 : 0) | (nb[r] << 32);
+                wa.keep_l[i] = w;
+                sum += w;
+                hits += h[r];
+            }
         }
         if (direct) {
             hits = block_sum(hits, sm);
@@ -1440,26 +1460,6 @@ __device__ __forceinline__ void d_merge_count(const ListView &L, DevStep *st, co
     }
     sum = block_sum(sum, sm);
     if (threadIdx.x == 0) wa.part[4 * blockIdx.x] = sum;
-}
-
-// exclusive prefixes of the keep flags in place
-__device__ __forceinline__ void d_keep_final(const DevStep *st, const WorkArrays &wa, int G)
-{
-    __shared__ i64 sm[32];
-    const bool second = blockIdx.x >= G;
-    const i64 n = second ? st->n_keys : st->n_occ;
-    i64 *f = second ? wa.keep_s : wa.keep_l;
-    i64 c = (n + G - 1) / G;
-    i64 b = second ? blockIdx.x - G : blockIdx.x;
-    i64 lo = b * c < n ? b * c : n, hi = lo + c < n ? lo + c : n;
-    i64 carry = wa.part[4 * blockIdx.x + 2];
-    for (i64 base = lo; base < hi; base += blockDim.x) {
-        i64 i = base + threadIdx.x;
-        i64 v = i < hi ? f[i] : 0, tot;
-        i64 incl = block_incl_scan(v, sm, tot);
-        if (i < hi) f[i] = carry + incl - v;
-        carry += tot;
-    }
 }
 
 // scan of the 2G partials: list part then spawn part
@@ -1477,38 +1477,6 @@ __device__ __forceinline__ void d_keep_top(DevStep *st, const WorkArrays &wa, in
         st->kept_list = ta & 0xFFFFFFFFLL;   // the low count of the packed list flags
         st->kept_new = tb;
     }
-}
-
-template <int K>
-__device__ __forceinline__ void d_scatter_list(const SysDev &s, const ListView &L, const ListView &O, DevStep *st, const WorkArrays &wa,
-                                                                const u64 *rkey)
-{
-    __shared__ i64 sm[32];
-    const i64 n = st->n_occ;
-    i64 asum = 0;
-    unsigned err = 0;
-    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
-        i64 v = wa.newpop[i];
-        if (!(i == 0 || v != 0)) continue;
-        // kept list entries before i, kept new keys before it (those inserted
-        // before earlier entries and those inserted right before i)
-        const i64 e = wa.keep_l[i];
-        const i64 out = (e & 0xFFFFFFFFLL) + (e >> 32) + wa.before[i];
-        if (out >= O.cap) {
-            err |= ERRB_LIST_OVERFLOW;
-            continue;
-        }
-        store_det<K>(O.bits, O.cap, out, load_det<K>(L.bits, L.cap, i));
-        O.key[out] = L.key[i];
-        O.pop[out] = v;
-        O.diag[out] = L.diag[i];
-        asum += v < 0 ? -v : v;
-    }
-    asum = block_sum(asum, sm);
-    if (threadIdx.x == 0) {
-        if (asum) atomicAdd((unsigned long long *)&st->ntot_after, (unsigned long long)asum);
-    }
-    if (err) atomicOr(&st->err, err);   // every thread reports its own bits
 }
 
 // The keep prefixes and the list's scatter in one pass.  Blocks [G, 2G):
@@ -1545,11 +1513,21 @@ __device__ __forceinline__ void d_keep_scatter(const ListView &L, const ListView
     unsigned err = 0;
     for (i64 base = lo; base < hi; base += ROWS * (i64)blockDim.x) {
         i64 w[ROWS], v[ROWS], e[ROWS];
+        Det<K> d[ROWS];
+        u64 key[ROWS];
+        double dg[ROWS];
+        // the entries' words are read with their counts (almost every entry
+        // is kept), so all reads of the four rows are in flight together
 #pragma unroll
         for (int r = 0; r < ROWS; r++) {
             const i64 i = base + r * (i64)blockDim.x + threadIdx.x;
             w[r] = i < hi ? wa.keep_l[i] : 0;
             v[r] = i < hi ? wa.newpop[i] : 0;
+            if (i < hi) {
+                d[r] = load_det<K>(L.bits, L.cap, i);
+                key[r] = L.key[i];
+                dg[r] = L.diag[i];
+            }
         }
 #pragma unroll
         for (int r = 0; r < ROWS; r++) {
@@ -1570,10 +1548,10 @@ __device__ __forceinline__ void d_keep_scatter(const ListView &L, const ListView
                 err |= ERRB_LIST_OVERFLOW;
                 continue;
             }
-            store_det<K>(O.bits, O.cap, out, load_det<K>(L.bits, L.cap, i));
-            O.key[out] = L.key[i];
+            store_det<K>(O.bits, O.cap, out, d[r]);
+            O.key[out] = key[r];
             O.pop[out] = v[r];
-            O.diag[out] = L.diag[i];
+            O.diag[out] = dg[r];
             asum += v[r] < 0 ? -v[r] : v[r];
         }
     }
@@ -1699,7 +1677,6 @@ __global__ void __launch_bounds__(WORK_THREADS) k_merge_match(const StepArgs *__
 __global__ void __launch_bounds__(SCAN_THREADS) k_merge_count(const StepArgs *__restrict__ A, int G);
 __global__ void __launch_bounds__(SCAN_THREADS) k_local_scan(const StepArgs *__restrict__ A);
 __global__ void __launch_bounds__(1024) k_keep_top(const StepArgs *__restrict__ A, int G);
-__global__ void __launch_bounds__(SCAN_THREADS) k_keep_final(const StepArgs *__restrict__ A, int G);
 __global__ void __launch_bounds__(1024) k_finalize(const StepArgs *__restrict__ A, int slots);
 
 template <int K, typename R>
@@ -1780,13 +1757,6 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_keep_scatter(const StepArgs *_
 {
     REPLICA;
     d_keep_scatter<K>(a.list[cur_], a.list[cur_ ^ 1], a.st, a.wa, G);
-}
-
-template <int K>
-__global__ void __launch_bounds__(WORK_THREADS) k_scatter_list(const StepArgs *__restrict__ A, int src)
-{
-    REPLICA;
-    d_scatter_list<K>(a.s, a.list[cur_], a.list[cur_ ^ 1], a.st, a.wa, a.sp.key[src ^ 1]);
 }
 
 template <int K, typename R>

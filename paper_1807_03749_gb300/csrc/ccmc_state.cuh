@@ -140,7 +140,7 @@ struct WorkArrays {
     i64 *part;        // block partials of the scans (4 per block)
     u64 *enum_part;   // 128-bit fixed-point E_num partial (lo, hi) per producing block
     i64 *newpop;      // list values after the merge (threshold applied)
-    i64 *keep_l;      // keep flag | before << 32 of list entries -> exclusive prefix (both counts)
+    i64 *keep_l;      // keep flag | before << 32 of list entries; exclusive prefix where new keys go in
     int *before;      // kept new keys inserted just before each list entry
     i64 *keep_s;      // keep flags of reduced spawns -> exclusive prefix
     i64 *ins;         // insertion position of a new key, -1 when matched

@@ -6,7 +6,7 @@
 //
 //  a1  k_scan_partial / k_scan_top           a7  k_sort_hist / scan / scatter
 //  a8  k_seg_count / k_part_scan / k_seg_write
-//  a9  k_merge_match / k_merge_count / k_keep_top / k_keep_final
+//  a9  k_merge_match / k_merge_count / k_keep_top (k_keep_scatter, k_scatter_new: per word count)
 //  a10 k_finalize      batch: k_sample_plan
 //  ccmc_reduce_records_noalloc (end of file): the sort and reduction as a
 //      standalone call on a static scratch array
@@ -132,12 +132,6 @@ __global__ void __launch_bounds__(1024) k_keep_top(const StepArgs *__restrict__ 
 {
     const StepArgs &a = A[blockIdx.y];
     d_keep_top(a.st, a.wa, G);
-}
-
-__global__ void __launch_bounds__(SCAN_THREADS) k_keep_final(const StepArgs *__restrict__ A, int G)
-{
-    const StepArgs &a = A[blockIdx.y];
-    d_keep_final(a.st, a.wa, G);
 }
 
 __global__ void __launch_bounds__(1024) k_finalize(const StepArgs *__restrict__ A, int slots)
