@@ -1426,32 +1426,18 @@ __device__ __forceinline__ void d_merge_count(const ListView &L, DevStep *st, co
         const u64 it = st->iter;
         const bool direct = st->nkb > 0;
         i64 hits = 0;   // entries that received directly added spawns: distinct keys of the step
-        constexpr int ROWS = 4;   // rows of the block whose reads are in flight together
-        for (i64 base = lo; base < hi; base += ROWS * (i64)blockDim.x) {
-            i64 v[ROWS], nb[ROWS], h[ROWS];
-#pragma unroll
-            for (int r = 0; r < ROWS; r++) {
-                const i64 i = base + r * (i64)blockDim.x + threadIdx.x;
-                v[r] = i < hi ? L.pop[i] + wa.death[i] + wa.acc[i] : 0;
-                nb[r] = i < hi ? wa.before[i] : 0;
-                h[r] = i < hi && direct ? wa.hit[i] : 0;
-            }
-#pragma unroll
-            for (int r = 0; r < ROWS; r++) {
-                const i64 i = base + r * (i64)blockDim.x + threadIdx.x;
-                if (i >= hi) continue;
-                // the key is read only for the few entries the threshold decides
-                const i64 av = v[r] < 0 ? -v[r] : v[r];
-                if (i > 0 && av > 0 && av < (i64)FIX_ONE) v[r] = threshold(p, it, L.key[i], v[r]);
-                wa.newpop[i] = v[r];
-                // two counts in one word (each below 2^31): the entry's keep
-                // flag and the kept new keys that go before it; one prefix
-                // gives both
-                const i64 w = ((i == 0 || v[r] != 0) ? 1 : 0) | (nb[r] << 32);
-                wa.keep_l[i] = w;
-                sum += w;
-                hits += h[r];
-            }
+        for (i64 i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            i64 v = L.pop[i] + wa.death[i] + wa.acc[i];
+            // the key is read only for the few entries the threshold decides
+            const i64 av = v < 0 ? -v : v;
+            if (i > 0 && av > 0 && av < (i64)FIX_ONE) v = threshold(p, it, L.key[i], v);
+            wa.newpop[i] = v;
+            // two counts in one word (each below 2^31): the entry's keep flag
+            // and the kept new keys that go before it; one prefix gives both
+            const i64 w = ((i == 0 || v != 0) ? 1 : 0) | ((i64)wa.before[i] << 32);
+            wa.keep_l[i] = w;
+            sum += w;
+            if (direct) hits += wa.hit[i];
         }
         if (direct) {
             hits = block_sum(hits, sm);
@@ -1482,8 +1468,8 @@ __device__ __forceinline__ void d_keep_top(DevStep *st, const WorkArrays &wa, in
 // The keep prefixes and the list's scatter in one pass.  Blocks [G, 2G):
 // exclusive prefix of the new keys' keep flags in place.  Blocks [0, G): the
 // exclusive prefix e of the packed list words (kept entries | kept new keys
-// before the entry << 32) over the block's chunk, four rows of the block in
-// flight at a time; each kept entry goes to e_lo + e_hi + (new keys right
+// before the entry << 32) over the block's chunk, four rows of counts read
+// before their scans; each kept entry goes to e_lo + e_hi + (new keys right
 // before it), and e is stored only where kept new keys are inserted (the
 // new-key scatter reads it there).
 template <int K>
@@ -1513,21 +1499,11 @@ __device__ __forceinline__ void d_keep_scatter(const ListView &L, const ListView
     unsigned err = 0;
     for (i64 base = lo; base < hi; base += ROWS * (i64)blockDim.x) {
         i64 w[ROWS], v[ROWS], e[ROWS];
-        Det<K> d[ROWS];
-        u64 key[ROWS];
-        double dg[ROWS];
-        // the entries' words are read with their counts (almost every entry
-        // is kept), so all reads of the four rows are in flight together
 #pragma unroll
         for (int r = 0; r < ROWS; r++) {
             const i64 i = base + r * (i64)blockDim.x + threadIdx.x;
             w[r] = i < hi ? wa.keep_l[i] : 0;
             v[r] = i < hi ? wa.newpop[i] : 0;
-            if (i < hi) {
-                d[r] = load_det<K>(L.bits, L.cap, i);
-                key[r] = L.key[i];
-                dg[r] = L.diag[i];
-            }
         }
 #pragma unroll
         for (int r = 0; r < ROWS; r++) {
@@ -1548,10 +1524,10 @@ __device__ __forceinline__ void d_keep_scatter(const ListView &L, const ListView
                 err |= ERRB_LIST_OVERFLOW;
                 continue;
             }
-            store_det<K>(O.bits, O.cap, out, d[r]);
-            O.key[out] = key[r];
+            store_det<K>(O.bits, O.cap, out, load_det<K>(L.bits, L.cap, i));
+            O.key[out] = L.key[i];
             O.pop[out] = v[r];
-            O.diag[out] = dg[r];
+            O.diag[out] = L.diag[i];
             asum += v[r] < 0 ? -v[r] : v[r];
         }
     }
