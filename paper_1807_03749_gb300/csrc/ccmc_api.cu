@@ -608,7 +608,7 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     Shapes &sh = ctx->sc.sh;
     sh.scan_grid = std::min(1024, 2 * nsm);
-    sh.work_grid = 8 * nsm;
+    sh.work_grid = 4 * nsm;   // one wave of the sampler and attempt kernels (four blocks per SM)
     sh.sort_grid = 2 * nsm;
     sh.key_bits = bits_for(key_bound);
     sh.digit_bits = params->radix_bits ? params->radix_bits : MAX_DIGIT_BITS;
