@@ -226,8 +226,9 @@ def summarize_ncu(csv_path: str, records_path: str, out_path: str, command: str)
         except ValueError:
             continue
         unit = r.get("Metric Unit", "")
-        scale = {"Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "byte": 1.0, "usecond": 1e-6, "msecond": 1e-3,
-                 "nsecond": 1e-9, "second": 1.0}.get(unit, 1.0)
+        scale = {"Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "byte": 1.0, "KB": 1e3, "MB": 1e6, "GB": 1e9, "B": 1.0,
+                 "usecond": 1e-6, "msecond": 1e-3, "nsecond": 1e-9, "second": 1.0, "us": 1e-6, "ms": 1e-3,
+                 "ns": 1e-9, "s": 1.0}.get(unit, 1.0)
         rows.setdefault(key, {})[r["Metric Name"]] = v * scale
     recs = json.load(open(records_path))
     rec = recs[0] if isinstance(recs, list) else recs
