@@ -659,6 +659,7 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     wa.keep_s = al.arr<i64>(sp.cap);
     wa.ins = al.arr<i64>(sp.cap);
     wa.part = al.arr<i64>(4 * 2 * (size_t)std::max(sh.scan_grid, sh.work_grid));
+    wa.wpart = al.arr<i64>(4 * (size_t)sh.scan_grid * (SCAN_THREADS / 32));
     wa.enum_part = al.arr<u64>(2 * (size_t)sh.enum_slots);
     wa.hist = al.arr<unsigned>((size_t)(1 << MAX_DIGIT_BITS) * sh.sort_grid);
     wa.hist_tot = al.arr<unsigned>((size_t)(1 << MAX_DIGIT_BITS));

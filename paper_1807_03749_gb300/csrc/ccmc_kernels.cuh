@@ -158,6 +158,18 @@ __device__ __forceinline__ void chunk_of(i64 n, i64 &lo, i64 &hi)
     if (hi > n) hi = n;
 }
 
+// Warp-granular chunks of a list: warp q of the grid's W warps gets
+// [q c, (q + 1) c), c = ceil(n / W); its scans need no block barrier.
+__device__ __forceinline__ i64 warp_chunk_of(i64 n, i64 &lo, i64 &hi)
+{
+    const i64 W = (i64)gridDim.x * (blockDim.x >> 5);
+    const i64 q = (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const i64 c = (n + W - 1) / W;
+    lo = q * c < n ? q * c : n;
+    hi = lo + c < n ? lo + c : n;
+    return q;
+}
+
 // All 32 lanes call; returns this lane's exclusive offset in a global
 // counter after reserving the warp's total with one atomic.
 __device__ __forceinline__ i64 warp_reserve(i64 *counter, i64 count)
@@ -588,37 +600,67 @@ __device__ __forceinline__ i64 threshold(const RunParams &p, u64 it, u64 key, i6
 
 __device__ __forceinline__ void d_scan_partial(const ListView &L, DevStep *st, const RunParams &p, const WorkArrays &wa)
 {
-    __shared__ i64 sm[32];
     i64 n = st->n_occ, lo, hi;
-    chunk_of(n, lo, hi);
+    const i64 q = warp_chunk_of(n, lo, hi);
     i64 sw = 0, sa = 0;
-    for (i64 i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    for (i64 i = lo + (threadIdx.x & 31); i < hi; i += 32) {
         i64 v = L.pop[i], av = v < 0 ? -v : v;
         if (i > 0) sw += av;
         if (p.fnc) sa += attempts_of(fabs((double)v / FIX_ONE), p);
     }
-    sw = block_sum(sw, sm);
-    sa = block_sum(sa, sm);
-    if (threadIdx.x == 0) {
-        wa.part[4 * blockIdx.x] = sw;
-        wa.part[4 * blockIdx.x + 1] = sa;
+    sw = warp_sum(sw);
+    sa = warp_sum(sa);
+    if ((threadIdx.x & 31) == 0) {
+        wa.wpart[4 * q] = sw;
+        wa.wpart[4 * q + 1] = sa;
     }
 }
 
-// one block of 1024 threads; grid <= 1024 partials
+// Exclusive prefixes of W warp partials (wpart[4 (off + q) + f] into
+// wpart[4 (off + q) + f + 2]) by one block of 1024 threads: warp v takes a
+// contiguous run, read 32 at a time (coalesced); the warps' totals are scanned
+// in shared memory.  Returns the grand total (every thread).
+__device__ __forceinline__ i64 partials_prefix(i64 *wpart, int off, int W, int f)
+{
+    __shared__ i64 s_tot[32];
+    __shared__ i64 s_all;
+    const int lane = threadIdx.x & 31, v = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int S = 32 * ((W + blockDim.x - 1) / blockDim.x);
+    const int s0 = v * S < W ? v * S : W, s1 = s0 + S < W ? s0 + S : W;
+    i64 tot = 0;
+    for (int j = s0; j < s1; j += 32) {
+        const int q = j + lane;
+        tot += warp_sum(q < s1 ? wpart[4 * (off + q) + f] : (i64)0);
+    }
+    __syncthreads();   // s_tot is free (an earlier call may still read it)
+    if (lane == 0) s_tot[v] = tot;
+    __syncthreads();
+    if (v == 0) {
+        const i64 x = lane < nwarp ? s_tot[lane] : 0;
+        const i64 incl = warp_incl_scan(x);
+        if (lane < nwarp) s_tot[lane] = incl - x;
+        if (lane == 31) s_all = incl;
+    }
+    __syncthreads();
+    i64 carry = s_tot[v];
+    for (int j = s0; j < s1; j += 32) {
+        const int q = j + lane;
+        const i64 x = q < s1 ? wpart[4 * (off + q) + f] : 0;
+        const i64 incl = warp_incl_scan(x);
+        if (q < s1) wpart[4 * (off + q) + f + 2] = carry + incl - x;
+        carry += __shfl_sync(FULLMASK, incl, 31);
+    }
+    return s_all;
+}
+
+// one block of 1024 threads over the W = grid x warps-per-block partials of
+// the warp-granular chunks
 __device__ __forceinline__ void d_scan_top(const ListView &L, DevStep *st, const RunParams &p, const WorkArrays &wa, int grid, int lmax)
 {
-    __shared__ i64 sm[32];
-    int t = threadIdx.x;
-    i64 sw = t < grid ? wa.part[4 * t] : 0;
-    i64 sa = t < grid ? wa.part[4 * t + 1] : 0;
-    i64 tw, ta;
-    i64 iw = block_incl_scan(sw, sm, tw);
-    i64 ia = block_incl_scan(sa, sm, ta);
-    if (t < grid) {
-        wa.part[4 * t + 2] = iw - sw;
-        wa.part[4 * t + 3] = ia - sa;
-    }
+    const int t = threadIdx.x;
+    const int W = grid * (SCAN_THREADS / 32);
+    const i64 tw = partials_prefix(wa.wpart, 0, W, 0);
+    i64 ta = p.fnc ? partials_prefix(wa.wpart, 0, W, 1) : 0;
     if (t == 0) {
         i64 n0 = st->n_occ > 0 ? L.pop[0] : 0;
         i64 an0 = n0 < 0 ? -n0 : n0;
@@ -725,18 +767,18 @@ __device__ __forceinline__ void d_scan_top(const ListView &L, DevStep *st, const
 template <int K, typename R>
 __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L, DevStep *st, const RunParams &p, const WorkArrays &wa)
 {
-    __shared__ i64 sm[32];
     __shared__ u64 smf[64];
     i64 n = st->n_occ, lo, hi;
-    chunk_of(n, lo, hi);
-    i64 cw = wa.part[4 * blockIdx.x + 2], ca = wa.part[4 * blockIdx.x + 3];
+    const i64 q = warp_chunk_of(n, lo, hi);
+    i64 cw = wa.wpart[4 * q + 2], ca = wa.wpart[4 * q + 3];
     const u64 it = st->iter;
     const double S = st->shift;
     Fix128 es = {0, 0};
     unsigned err = 0;
     const bool kb = st->nkb > 0;
-    for (i64 base = lo; base < hi; base += blockDim.x) {
-        i64 i = base + threadIdx.x;
+    // each warp scans its own chunk 32 entries at a time (no block barrier)
+    for (i64 base = lo; base < hi; base += 32) {
+        i64 i = base + (threadIdx.x & 31);
         bool ok = i < hi;
         // every read of the entry is issued before the block scans, so that
         // one memory latency per tile is exposed instead of two
@@ -748,9 +790,13 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
         i64 w = (ok && i > 0) ? av : 0;
         double amp = (double)v / FIX_ONE;
         i64 na = (ok && p.fnc) ? attempts_of(fabs(amp), p) : 0;
-        i64 tw, ta = 0, ia = 0;
-        i64 iw = block_incl_scan(w, sm, tw);
-        if (p.fnc) ia = block_incl_scan(na, sm, ta);   // attempt prefix: full non-composite visits only
+        i64 ta = 0, ia = 0;
+        const i64 iw = warp_incl_scan(w);
+        const i64 tw = __shfl_sync(FULLMASK, iw, 31);
+        if (p.fnc) {   // attempt prefix: full non-composite visits only
+            ia = warp_incl_scan(na);
+            ta = __shfl_sync(FULLMASK, ia, 31);
+        }
         if (ok) {
             PickEntry pe;
             pe.prefix = cw + iw;

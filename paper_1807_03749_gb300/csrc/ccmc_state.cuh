@@ -138,6 +138,7 @@ struct WorkArrays {
     int kbucket_bits; // log2 of the key-bucket capacity
     unsigned char *hit;  // list entries that received directly added spawns this step
     i64 *part;        // block partials of the scans (4 per block)
+    i64 *wpart;       // warp partials of the list scan (4 per warp of the scan grid)
     u64 *enum_part;   // 128-bit fixed-point E_num partial (lo, hi) per producing block
     i64 *newpop;      // list values after the merge (threshold applied)
     i64 *keep_l;      // keep flag | before << 32 of list entries; exclusive prefix where new keys go in
