@@ -643,7 +643,7 @@ ccmc_status ccmc_init(const ccmc_hamiltonian *ham, const ccmc_reference *ref, in
     const i64 lc = ctx->list_cap;
     wa.picks = al.arr<PickEntry>(lc);
     wa.bucket_bits = 10;
-    while (wa.bucket_bits < 22 && (1LL << wa.bucket_bits) < lc / 2) wa.bucket_bits++;
+    while (wa.bucket_bits < 24 && (1LL << wa.bucket_bits) < lc / 2) wa.bucket_bits++;
     wa.bucket = al.arr<int>(((size_t)1 << wa.bucket_bits) + 1);
     wa.att_end = al.arr<i64>(lc);
     wa.catt = al.arr<double>(lc);
