@@ -131,3 +131,32 @@ def test_summarize_ncu_per_unit_figures(tmp_path):
     assert float(got["sample"][6]) == 16.0
     # the sort: two kernels summed, the longest named, issue weighted by time
     assert float(got["sort"][3]) == 7e6 / 400 and abs(float(got["sort"][5]) - 30.0) < 1e-9
+
+
+def test_summarize_ncu_short_unit_names(tmp_path):
+    """ncu's --csv log file may print short units (ns, MB, byte): the summary's
+    per-unit bytes and the launch list's microseconds are the same."""
+    import json
+
+    hdr = '"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size","Grid Size",' \
+          '"Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"\n'
+    name = "void ccmc::k_sample<2, double, 0>(const ccmc::StepArgs *, int)"
+    rows = []
+    for metric, unit, value in [("gpu__time_duration.sum", "ns", 2500000), ("dram__bytes_read.sum", "MB", 10.0),
+                                ("dram__bytes_write.sum", "byte", 2e6), ("smsp__inst_executed.sum", "inst", 100.0),
+                                ("smsp__thread_inst_executed.sum", "inst", 1600.0),
+                                ("smsp__issue_active.avg.pct_of_peak_sustained_active", "%", 50.0)]:
+        rows.append(f'"0","1","python","h","{name}","1","7","(256, 1, 1)","(608, 1, 1)","0","10.3","",'
+                    f'"{metric}","{unit}","{value}"\n')
+    csvp = tmp_path / "l.csv"
+    csvp.write_text(hdr + "".join(rows))
+    rec = dict(n_sel=1000, n_visit=0, n_attempts=900, n_spawned=400, n_direct=0, n_keys=50, nocc_after=300)
+    recp = tmp_path / "r.json"
+    recp.write_text(json.dumps([rec]))
+    out = tmp_path / "traffic_toy.txt"
+    bench.summarize_ncu(str(csvp), str(recp), str(out), "ncu ... python bench.py")
+    text = out.read_text()
+    got = {ln.split()[0]: ln.split() for ln in text.splitlines() if not ln.startswith("#")}
+    assert float(got["sample"][3]) == 12e6 / 1000
+    launch = [ln for ln in text.splitlines() if ln.startswith("#   k_sample")][0].split()
+    assert float(launch[-3]) == 2500.0   # microseconds (the name holds spaces: count from the right)
