@@ -780,7 +780,7 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
     for (i64 base = lo; base < hi; base += 32) {
         i64 i = base + (threadIdx.x & 31);
         bool ok = i < hi;
-        // every read of the entry is issued before the block scans, so that
+        // every read of the entry is issued before the warp scans, so that
         // one memory latency per tile is exposed instead of two
         i64 v = ok ? L.pop[i] : 0, av = v < 0 ? -v : v;
         const u64 key_i = ok && kb ? L.key[i] : 0, key_p = ok && kb && i > 0 ? L.key[i - 1] : 0;
