@@ -661,9 +661,10 @@ def run_gpu(args, w, dist, rank, world, local):
         ctx.set_list(bits, pop)
         h2d += bits.nbytes + pop.nbytes
         ctx.step(1)
-        bits, keys_h, pop = ctx.get_list(out=bufs[(k + 1) % 2])
+        # the list and the estimators come back; its keys are recomputed on upload
+        bits, _, pop = ctx.get_list(out=bufs[(k + 1) % 2], with_keys=False)
         ctx.energy()
-        d2h += bits.nbytes + keys_h.nbytes + pop.nbytes + 40
+        d2h += bits.nbytes + pop.nbytes + 40
     torch.cuda.synchronize()
     e2e_secs = time.perf_counter() - t0
     e2e_samples = sum(r["n_sel"] + r["n_visit"] for r in ctx.records()[-args.e2e_steps:])
@@ -883,10 +884,10 @@ def run_gpu_batched(args, local):
                 c.set_list(bits, pop)
                 h2d += bits.nbytes + pop.nbytes
             batch.step(1)
-            lists = [c.get_list(out=b) for c, b in zip(ctxs, bufs[(k + 1) % 2])]
-            for c, (bits, kk, pop) in zip(ctxs, lists):
+            lists = [c.get_list(out=b, with_keys=False) for c, b in zip(ctxs, bufs[(k + 1) % 2])]
+            for c, (bits, _, pop) in zip(ctxs, lists):
                 c.energy()
-                d2h += bits.nbytes + kk.nbytes + pop.nbytes + 40
+                d2h += bits.nbytes + pop.nbytes + 40
         torch.cuda.synchronize()
         e2e_secs = time.perf_counter() - t0
         e2e_samples = sum(r["n_sel"] + r["n_visit"] for c in ctxs for r in c.records()[-args.e2e_steps:])

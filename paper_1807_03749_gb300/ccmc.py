@@ -234,26 +234,29 @@ class Context:
         self._check(self._lib.ccmc_list_size(self._h, ctypes.byref(n)))
         return n.value
 
-    def get_list(self, out=None):
+    def get_list(self, out=None, with_keys: bool = True):
         """(bits[n, K] uint64, keys[n] uint64, pop[n] int64) in key order.
         With out = (bits, keys, pop) of room for the list (for instance pinned
         host buffers), those are filled and views of their first n rows
-        returned."""
+        returned.  with_keys=False skips the keys (None in their place): a
+        list uploaded again with set_list has its keys recomputed anyway."""
         n = self.list_size()
         if out is None:
             bits = np.zeros((n, self.nw), dtype=np.uint64)
-            keys = np.zeros(n, dtype=np.uint64)
+            keys = np.zeros(n, dtype=np.uint64) if with_keys else None
             pop = np.zeros(n, dtype=np.int64)
         else:
             bits, keys, pop = out
-            if len(pop) < n or len(keys) < n or bits.shape[0] < n or bits.shape[1] != self.nw:
+            if not with_keys:
+                keys = None
+            if len(pop) < n or (keys is not None and len(keys) < n) or bits.shape[0] < n or bits.shape[1] != self.nw:
                 raise ValueError("output buffers too small")
-            if not (bits.flags.c_contiguous and keys.flags.c_contiguous and pop.flags.c_contiguous):
+            if not (bits.flags.c_contiguous and pop.flags.c_contiguous and (keys is None or keys.flags.c_contiguous)):
                 raise ValueError("output buffers must be contiguous")
         m = c_size_t(0)
-        self._check(self._lib.ccmc_get_list(self._h, _ptr(bits, c_uint64), _ptr(keys, c_uint64), _ptr(pop, c_int64),
-                                            n, ctypes.byref(m)))
-        return bits[:n], keys[:n], pop[:n]
+        kp = _ptr(keys, c_uint64) if keys is not None else None
+        self._check(self._lib.ccmc_get_list(self._h, _ptr(bits, c_uint64), kp, _ptr(pop, c_int64), n, ctypes.byref(m)))
+        return bits[:n], (keys[:n] if keys is not None else None), pop[:n]
 
     def set_list(self, bits: np.ndarray, pop: np.ndarray):
         bits = np.ascontiguousarray(bits, dtype=np.uint64).reshape(-1, self.nw)

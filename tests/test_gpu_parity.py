@@ -573,3 +573,15 @@ def test_torch_allocator_and_stream(ccmc):
     s = torch.cuda.Stream()
     so, sim, ctx = _pair(ccmc, w, use_torch_allocator=True, stream=s.cuda_stream)
     _run_lockstep(sim, ctx, 30, check_spawned_every=10)
+
+
+def test_get_list_without_keys(ccmc):
+    """The list download can skip the keys (a NULL buffer at the ABI): the
+    bit strings and populations are the same as with them."""
+    w = workload("ueg14_m38_ccsd")
+    ctx = ccmc.from_workload(w)
+    ctx.step(50)
+    bits, keys, pop = ctx.get_list()
+    b2, k2, p2 = ctx.get_list(with_keys=False)
+    assert k2 is None and np.array_equal(bits, b2) and np.array_equal(pop, p2) and len(keys) == len(pop)
+    ctx.close()
