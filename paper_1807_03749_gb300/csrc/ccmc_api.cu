@@ -194,6 +194,8 @@ struct Alloc {
 
 }  // namespace
 
+constexpr int UPLOAD_CHUNKS = 8;   // pieces of a list upload whose copy and check overlap
+
 struct ccmc_ctx {
     HostSys hs;
     StepCtx sc;
@@ -221,6 +223,10 @@ struct ccmc_ctx {
     // the validation word of the last upload
     u64 *io = nullptr;
     unsigned *d_bad = nullptr, *h_bad = nullptr;
+    // chunked upload: the copies run on their own stream, each chunk's check
+    // on the context's stream once its copy has landed (created on first use)
+    cudaStream_t up_stream = nullptr;
+    cudaEvent_t up_ev[UPLOAD_CHUNKS + 1] = {};
     // the batch that steps this context, if any (it is not stepped alone
     // then), and the stream its batched steps run on
     ccmc_batch *batch = nullptr;
@@ -279,11 +285,11 @@ enum : unsigned {
 // zero total momentum for the gas, truncation level, HF first), then its
 // key and diagonal energy.
 template <int K, typename R>
-__global__ void k_load_list(SysDev s, ListView L, const u64 *rows, i64 n, unsigned *bad)
+__global__ void k_load_list(SysDev s, ListView L, const u64 *rows, i64 i0, i64 i1, unsigned *bad)
 {
     const u64 alpha = 0x5555555555555555ULL;
     unsigned b = 0;
-    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+    for (i64 i = i0 + (i64)blockIdx.x * blockDim.x + threadIdx.x; i < i1; i += (i64)gridDim.x * blockDim.x) {
         Det<K> d;
         int pc = 0, na = 0, holes = 0, kx = 0, ky = 0, kz = 0;
         unsigned e = 0;
@@ -342,30 +348,31 @@ __global__ void k_store_list(ListView L, u64 *rows, i64 n)
         for (int w = 0; w < K; w++) rows[i * K + w] = L.bits[w * L.cap + i];
 }
 
-cudaError_t load_list(ccmc_ctx *ctx, ListView &L, i64 n)
+// the device check of entries [i0, i1) of an upload (key and Delta E computed)
+cudaError_t load_list(ccmc_ctx *ctx, ListView &L, i64 i0, i64 i1)
 {
+    const i64 n = i1 - i0;
     const int g = (int)std::min<i64>(4096, (n + 255) / 256 + 1);
     const bool f = ctx->sc.fp32;
     cudaStream_t sm = ctx->stream;
     const SysDev &s = ctx->sc.sys;
     switch (ctx->sc.K) {
     case 1:
-        if (f) k_load_list<1, float><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad);
-        else k_load_list<1, double><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad);
+        if (f) k_load_list<1, float><<<g, 256, 0, sm>>>(s, L, ctx->io, i0, i1, ctx->d_bad);
+        else k_load_list<1, double><<<g, 256, 0, sm>>>(s, L, ctx->io, i0, i1, ctx->d_bad);
         break;
     case 2:
-        if (f) k_load_list<2, float><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad);
-        else k_load_list<2, double><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad);
+        if (f) k_load_list<2, float><<<g, 256, 0, sm>>>(s, L, ctx->io, i0, i1, ctx->d_bad);
+        else k_load_list<2, double><<<g, 256, 0, sm>>>(s, L, ctx->io, i0, i1, ctx->d_bad);
         break;
     case 3:
-        if (f) k_load_list<3, float><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad);
-        else k_load_list<3, double><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad);
+        if (f) k_load_list<3, float><<<g, 256, 0, sm>>>(s, L, ctx->io, i0, i1, ctx->d_bad);
+        else k_load_list<3, double><<<g, 256, 0, sm>>>(s, L, ctx->io, i0, i1, ctx->d_bad);
         break;
-    case 4: k_load_list<4, double><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad); break;   // FP64 only
-    case 5: k_load_list<5, double><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad); break;
-    default: k_load_list<6, double><<<g, 256, 0, sm>>>(s, L, ctx->io, n, ctx->d_bad); break;
+    case 4: k_load_list<4, double><<<g, 256, 0, sm>>>(s, L, ctx->io, i0, i1, ctx->d_bad); break;   // FP64 only
+    case 5: k_load_list<5, double><<<g, 256, 0, sm>>>(s, L, ctx->io, i0, i1, ctx->d_bad); break;
+    default: k_load_list<6, double><<<g, 256, 0, sm>>>(s, L, ctx->io, i0, i1, ctx->d_bad); break;
     }
-    k_check_order<<<g, 256, 0, sm>>>(L.key, n, ctx->d_bad);
     return cudaGetLastError();
 }
 
@@ -752,9 +759,31 @@ ccmc_status ccmc_set_list(ccmc_ctx *ctx, const uint64_t *bits, const int64_t *po
     const int nb = ctx->sc.cur ^ 1;
     ListView &L = ctx->sc.list[nb];
     CK(cudaMemsetAsync(ctx->d_bad, 0, sizeof(unsigned), ctx->stream));
-    CK(cudaMemcpyAsync(ctx->io, bits, n * (size_t)K * sizeof(u64), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(L.pop, pop, n * sizeof(i64), cudaMemcpyHostToDevice, ctx->stream));
-    CK(load_list(ctx, L, (i64)n));
+    if (!ctx->up_stream) {
+        CK(cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking));
+        for (int c = 0; c <= UPLOAD_CHUNKS; c++) CK(cudaEventCreateWithFlags(&ctx->up_ev[c], cudaEventDisableTiming));
+    }
+    // the copies start after the context's earlier work (which may still use
+    // the staging rows and the spare list); the check of each piece waits
+    // for its copy, so copies of later pieces overlap checks of earlier ones
+    CK(cudaEventRecord(ctx->up_ev[UPLOAD_CHUNKS], ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->up_stream, ctx->up_ev[UPLOAD_CHUNKS], 0));
+    const i64 chunk = std::max<i64>(1 << 20, ((i64)n + UPLOAD_CHUNKS - 1) / UPLOAD_CHUNKS);
+    int c = 0;
+    for (i64 a = 0; a < (i64)n; a += chunk, c++) {
+        const i64 m = std::min<i64>(chunk, (i64)n - a);
+        CK(cudaMemcpyAsync(ctx->io + a * K, bits + a * K, (size_t)m * K * sizeof(u64), cudaMemcpyHostToDevice,
+                           ctx->up_stream));
+        CK(cudaMemcpyAsync(L.pop + a, pop + a, (size_t)m * sizeof(i64), cudaMemcpyHostToDevice, ctx->up_stream));
+        CK(cudaEventRecord(ctx->up_ev[c], ctx->up_stream));
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->up_ev[c], 0));
+        CK(load_list(ctx, L, a, a + m));
+    }
+    {
+        const int g = (int)std::min<i64>(4096, ((i64)n + 255) / 256 + 1);
+        k_check_order<<<g, 256, 0, ctx->stream>>>(L.key, (i64)n, ctx->d_bad);
+        CK(cudaGetLastError());
+    }
     CK(cudaMemcpyAsync(ctx->h_bad, ctx->d_bad, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     const unsigned bad = *ctx->h_bad;
@@ -1103,6 +1132,12 @@ void ccmc_free(ccmc_ctx *ctx)
     ctx->al.release();
     for (int e = 0; e < 8; e++)
         if (ctx->sc.events[e]) cudaEventDestroy(ctx->sc.events[e]);
+    if (ctx->up_stream) {
+        cudaStreamSynchronize(ctx->up_stream);
+        cudaStreamDestroy(ctx->up_stream);
+    }
+    for (int c = 0; c <= UPLOAD_CHUNKS; c++)
+        if (ctx->up_ev[c]) cudaEventDestroy(ctx->up_ev[c]);
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
     if (ctx->h_shift) cudaFreeHost(ctx->h_shift);
     if (ctx->h_bad) cudaFreeHost(ctx->h_bad);
