@@ -62,12 +62,14 @@ def shoulder_of(ntot, n0, window: int = 20, drop: float = 0.9) -> dict:
 
 
 def run_sampler(ccmc, w: dict, fnc: bool, ms: bool, tau: float, d0: float, cap: float, max_steps: int,
-                stream=None, chunk: int = 10):
+                stream=None, chunk: int = 10, seed: int = 0):
     """Grows one run at a constant shift from d0 particles on the reference
     until N_total exceeds cap (or max_steps); returns per-step (N_total, N_0)
     after each step and how the run ended."""
     # the shift would start to vary only past 2 x cap; the run stops at cap
     over = dict(tau=tau, d0_init=d0, target_pop=2.0 * cap, fnc=fnc, multispawn=ms)
+    if seed:
+        over["seed"] = seed
     w = {k: v for k, v in w.items() if k != "list_capacity"}   # capacities follow the target
     ctx = ccmc.from_workload(w, stream=stream, **over)
     ntot, n0 = [], []
@@ -97,6 +99,8 @@ def main():
     ap.add_argument("--samplers", default=",".join(SAMPLERS))
     ap.add_argument("--eri-scale", type=float, default=0.0, help="molecule only: scale of the two-electron integrals")
     ap.add_argument("--series", action="store_true", help="include the per-step series in the output")
+    ap.add_argument("--seeds", default="", help="comma-separated Philox seeds: one run per seed and sampler, "
+                                                "with the mean and spread of the shoulder heights")
     args = ap.parse_args()
     import paper_1807_03749_gb300 as ccmc
     from ccmc_inputs import workload
@@ -106,15 +110,27 @@ def main():
         w["eri_scale"] = args.eri_scale
     out = {"workload": args.workload, "tau": args.tau, "d0": args.d0, "cap": args.cap,
            "eri_scale": w.get("eri_scale", 1.0), "runs": {}}
+    seeds = [int(x) for x in args.seeds.split(",")] if args.seeds else [0]
     for name in args.samplers.split(","):
         fnc, ms = SAMPLERS[name]
-        ntot, n0, status = run_sampler(ccmc, w, fnc, ms, args.tau, args.d0, args.cap, args.max_steps)
-        res = dict(shoulder_of(ntot, n0, args.window), steps=len(ntot), status=status,
-                   n_total_last=ntot[-1] if ntot else None, n0_last=n0[-1] if n0 else None)
-        if args.series:
-            res["n_total"], res["n0"] = ntot, n0
-        out["runs"][name] = res
-        print(json.dumps({name: {k: v for k, v in res.items() if k not in ("n_total", "n0")}}), flush=True)
+        per_seed = []
+        for seed in seeds:
+            ntot, n0, status = run_sampler(ccmc, w, fnc, ms, args.tau, args.d0, args.cap, args.max_steps, seed=seed)
+            res = dict(shoulder_of(ntot, n0, args.window), steps=len(ntot), status=status, seed=seed,
+                       n_total_last=ntot[-1] if ntot else None, n0_last=n0[-1] if n0 else None)
+            if args.series:
+                res["n_total"], res["n0"] = ntot, n0
+            per_seed.append(res)
+            print(json.dumps({name: {k: v for k, v in res.items() if k not in ("n_total", "n0")}}), flush=True)
+        out["runs"][name] = per_seed if len(seeds) > 1 else per_seed[0]
+        found = [r["ratio"] for r in per_seed if r["found"]]
+        if len(seeds) > 1 and found:
+            import numpy as np
+
+            out.setdefault("summary", {})[name] = {
+                "found": len(found), "of": len(seeds), "ratio_mean": float(np.mean(found)),
+                "ratio_sd": float(np.std(found, ddof=1)) if len(found) > 1 else None}
+            print(json.dumps({name: out["summary"][name]}), flush=True)
     print(json.dumps(out), flush=True)
 
 
