@@ -996,7 +996,7 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
                     for (int e = 1; e < sz; e++) {
                         u64 rr = e < 2 ? r0.v[2 + e] : r1.v[e - 2];
                         idx[e] = local_pick(wa, pk, n, lcs, nlc, q, below(rr, (u64)nq));
-                        if (idx[e] < 0) {
+                        if (idx[e] < 0) {   // tables inconsistent (cannot happen): a sticky error, not a guess
                             valid = false;
                             err |= ERRB_NUMERIC;
                         }
