@@ -770,14 +770,21 @@ ccmc_status ccmc_set_list(ccmc_ctx *ctx, const uint64_t *bits, const int64_t *po
     CK(cudaStreamWaitEvent(ctx->up_stream, ctx->up_ev[UPLOAD_CHUNKS], 0));
     const i64 chunk = std::max<i64>(1 << 20, ((i64)n + UPLOAD_CHUNKS - 1) / UPLOAD_CHUNKS);
     int c = 0;
-    for (i64 a = 0; a < (i64)n; a += chunk, c++) {
+    cudaError_t ue = cudaSuccess;
+    for (i64 a = 0; a < (i64)n && ue == cudaSuccess; a += chunk, c++) {
         const i64 m = std::min<i64>(chunk, (i64)n - a);
-        CK(cudaMemcpyAsync(ctx->io + a * K, bits + a * K, (size_t)m * K * sizeof(u64), cudaMemcpyHostToDevice,
-                           ctx->up_stream));
-        CK(cudaMemcpyAsync(L.pop + a, pop + a, (size_t)m * sizeof(i64), cudaMemcpyHostToDevice, ctx->up_stream));
-        CK(cudaEventRecord(ctx->up_ev[c], ctx->up_stream));
-        CK(cudaStreamWaitEvent(ctx->stream, ctx->up_ev[c], 0));
-        CK(load_list(ctx, L, a, a + m));
+        ue = cudaMemcpyAsync(ctx->io + a * K, bits + a * K, (size_t)m * K * sizeof(u64), cudaMemcpyHostToDevice,
+                             ctx->up_stream);
+        if (ue == cudaSuccess)
+            ue = cudaMemcpyAsync(L.pop + a, pop + a, (size_t)m * sizeof(i64), cudaMemcpyHostToDevice, ctx->up_stream);
+        if (ue == cudaSuccess) ue = cudaEventRecord(ctx->up_ev[c], ctx->up_stream);
+        if (ue == cudaSuccess) ue = cudaStreamWaitEvent(ctx->stream, ctx->up_ev[c], 0);
+        if (ue == cudaSuccess) ue = load_list(ctx, L, a, a + m);
+    }
+    if (ue != cudaSuccess) {
+        // no copy may still read the caller's buffers once the call returns
+        cudaStreamSynchronize(ctx->up_stream);
+        return cuda_fail(ctx, ue, "list upload");
     }
     {
         const int g = (int)std::min<i64>(4096, ((i64)n + 255) / 256 + 1);
