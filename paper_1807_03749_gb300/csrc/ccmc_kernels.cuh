@@ -256,6 +256,21 @@ __device__ __forceinline__ bool round_value(double x, u64 r, const RunParams &p,
     return stoch_round(x, unif(r), spawn ? p.spawn_cutoff : 0.0, out);
 }
 
+// the determinant of a picked entry: from its pick row (one granule with
+// the prefix and population just searched) when it has at most four words
+template <int K>
+__device__ __forceinline__ Det<K> pick_det(const PickEntry *pk, const ListView &L, i64 id)
+{
+    Det<K> d;
+    if constexpr (K <= 4) {
+#pragma unroll
+        for (int w = 0; w < K; w++) d.w[w] = __ldg(&pk[id].w[w]);
+    } else {
+        d = load_det<K>(L.bits, L.cap, id);
+    }
+    return d;
+}
+
 // smallest i in [1, n-1] with prefix[i] > x (excitor owning position x);
 // the bucket of x brackets the answer between the owners of its first
 // position and of the next bucket's first position
@@ -837,6 +852,8 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
                 const int lev = level_of(s, d);
                 pe.href = (lev == 1 || lev == 2) ? h_ref<K, R>(s, d) : 0.0;
             }
+#pragma unroll
+            for (int q = 0; q < 4; q++) pe.w[q] = q < K ? d.w[q < K ? q : 0] : 0;
             wa.picks[i] = pe;
             wa.death[i] = dv;
         }
@@ -1010,13 +1027,13 @@ __device__ __forceinline__ void d_sample(const SysDev &s, const ListView &L, Dev
                     // applying it to HF (the closed form of the same product)
                     const i64 id = idx[0];
                     if (__ldg(&pk[id].pop) < 0) neg ^= 1;
-                    dj = load_det<K>(L.bits, L.cap, id);
+                    dj = pick_det<K>(pk, L, id);
                     par = excitor_sign(s, dj) < 0 ? 1 : 0;
                 } else {
                     for (int e = 0; e < sz && valid; e++) {
                         const i64 id = idx[e];
                         if (__ldg(&pk[id].pop) < 0) neg ^= 1;
-                        const Det<K> de = load_det<K>(L.bits, L.cap, id);
+                        const Det<K> de = pick_det<K>(pk, L, id);
                         if (!apply_excitor(s, de, dj, par)) valid = false;   // shared orbital
                     }
                 }

@@ -117,13 +117,14 @@ struct ClusterBuf {
 // The cluster sampler's view of one list entry besides its bit string,
 // written by the scans each step and gathered by a pick as one 32-byte
 // sector: selection prefix, population, death factor and <HF|H|D>.
-struct __align__(32) PickEntry {
+struct __align__(64) PickEntry {
     i64 prefix;     // inclusive |pop| prefix over entries >= 1 (entry 0: 0)
     i64 pop;
     double tdeath;  // tau (Delta E_i - S): the death factor of this step
     double href;    // <HF|H|D_i> (levels 1-2; 0 otherwise; 0 with full non-composite sampling)
+    u64 w[4];       // the determinant's words (up to four; more are read from the list)
 };
-static_assert(sizeof(PickEntry) == 32, "pick table rows are one 32-byte sector");
+static_assert(sizeof(PickEntry) == 64, "pick table rows are one 64-byte granule");
 
 // Per-step work arrays over the list and the merge.
 struct WorkArrays {
