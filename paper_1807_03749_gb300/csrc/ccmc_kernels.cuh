@@ -852,6 +852,7 @@ __device__ __forceinline__ void d_scan_final(const SysDev &s, const ListView &L,
                 const int lev = level_of(s, d);
                 pe.href = (lev == 1 || lev == 2) ? h_ref<K, R>(s, d) : 0.0;
             }
+            // the words ride in the row a pick reads anyway (up to four)
 #pragma unroll
             for (int q = 0; q < 4; q++) pe.w[q] = q < K ? d.w[q < K ? q : 0] : 0;
             wa.picks[i] = pe;
